@@ -1,0 +1,411 @@
+/*
+ * nomad_oracle.c -- serial CPU oracle for NOMAD matrix completion
+ * (Yun, Yu, Hsieh, Vishwanathan, Dhillon, "NOMAD: Non-locking, stOchastic
+ * Multi-machine algorithm for Asynchronous and Decentralized matrix
+ * completion", arXiv 1312.0193).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load this library.
+ * It shares no source, header, table or helper with the CUDA path.
+ *
+ * Everything here is deliberately plain: one rating at a time, in the order
+ * the paper states, in IEEE binary64 unless a function says otherwise.
+ * Build with -ffp-contract=off so that no multiply-add is fused behind the
+ * reader's back.
+ *
+ * Readings of the paper that this file commits to (each also listed in the
+ * design notes of the repository):
+ *  R1  Sign of the SGD step (Sec. 2.3, Eq. w_update / h_update).  The
+ *      derivative of 1/2 (A_ij - <w_i,h_j>)^2 w.r.t. w_i is -(A_ij-<w,h>) h_j,
+ *      so a descent step is  w_i += s (e h_j - lambda w_i),
+ *      h_j += s (e w_i - lambda h_j)  with  e = A_ij - <w_i,h_j>.
+ *  R2  The "w_j" inside the printed h-update is a typo for w_i.
+ *  R3  Both updates use the OLD w_i (one gradient evaluation per rating).
+ *      The alternative (h-update sees the new w_i) is available through the
+ *      flag h_uses_new_w so that the choice is explicit and testable.
+ *  R4  t in the step size (Sec. 5.1, Eq. stepsize_method) counts the updates
+ *      already applied to the rating (i,j); the first visit uses s_0 = alpha.
+ *  R5  The regulariser is applied per rating with plain lambda (the
+ *      simplified form of Eq. obj_fcn): no division by |Omega_i|.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,       */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11).  Used for the     */
+/* factor initialisation of Alg. 1 and for every random draw of the oracle. */
+/* ------------------------------------------------------------------------ */
+static const uint32_t PHILOX_MUL_A = 0xD2511F53u;
+static const uint32_t PHILOX_MUL_B = 0xCD9E8D57u;
+static const uint32_t PHILOX_KEY_STEP_A = 0x9E3779B9u; /* golden ratio */
+static const uint32_t PHILOX_KEY_STEP_B = 0xBB67AE85u; /* sqrt(3) - 1 */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { /* the key is bumped before every round but the first */
+      k0 += PHILOX_KEY_STEP_A;
+      k1 += PHILOX_KEY_STEP_B;
+    }
+    uint64_t prod_a = (uint64_t)PHILOX_MUL_A * (uint64_t)x0;
+    uint64_t prod_b = (uint64_t)PHILOX_MUL_B * (uint64_t)x2;
+    uint32_t hi_a = (uint32_t)(prod_a >> 32), lo_a = (uint32_t)prod_a;
+    uint32_t hi_b = (uint32_t)(prod_b >> 32), lo_b = (uint32_t)prod_b;
+    uint32_t y0 = hi_b ^ x1 ^ k0;
+    uint32_t y1 = lo_b;
+    uint32_t y2 = hi_a ^ x3 ^ k1;
+    uint32_t y3 = lo_a;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* One 32-bit word of the stream (seed; c0,c1,c2,c3), word index w in 0..3. */
+static uint32_t rand_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                          uint32_t c3, int w) {
+  uint32_t ctr[4] = {c0, c1, c2, c3};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  return out[w];
+}
+
+/* Uniform integer in [0, bound) from one 32-bit word (multiply-shift). */
+static uint32_t bounded(uint32_t word, uint32_t bound) {
+  return (uint32_t)(((uint64_t)word * (uint64_t)bound) >> 32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initialisation (Alg. 1 "initialize parameters"; Sec. 5.1 set-up):        */
+/* every entry of W and H independent UniformReal(0, 1/sqrt(k)).            */
+/*                                                                          */
+/* Entry (r, l) of the factor `which` (0 = W, 1 = H) takes word (l mod 4)   */
+/* of Philox4x32-10 with key = seed and counter = (l/4, r_lo, r_hi, which). */
+/* u = (word >> 8) * 2^-24 is exact in binary32; the entry is the binary32  */
+/* product u * c with c = binary32(1/sqrt(k)), stored here widened to       */
+/* double (the widening is exact).                                          */
+/* ------------------------------------------------------------------------ */
+void orc_init_factor(int64_t rows, int32_t k, uint64_t seed, uint32_t which,
+                     double *F) {
+  const float c = (float)(1.0 / sqrt((double)k));
+  for (int64_t r = 0; r < rows; ++r) {
+    for (int32_t l = 0; l < k; ++l) {
+      uint32_t word = rand_word(seed, (uint32_t)(l / 4), (uint32_t)r,
+                                (uint32_t)((uint64_t)r >> 32), which, l % 4);
+      float u = (float)(word >> 8) * (1.0f / 16777216.0f);
+      float v = u * c; /* one binary32 rounding */
+      F[r * (int64_t)k + l] = (double)v;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step size, Sec. 5.1 Eq. stepsize_method: s_t = alpha / (1 + beta t^1.5). */
+/* ------------------------------------------------------------------------ */
+double orc_step_size(double alpha, double beta, int64_t t) {
+  return alpha / (1.0 + beta * pow((double)t, 1.5));
+}
+
+/* ------------------------------------------------------------------------ */
+/* One SGD update on rating (i,j) with value a (Sec. 2.3, Eq. w_update and  */
+/* h_update under readings R1-R3).                                          */
+/* ------------------------------------------------------------------------ */
+void orc_sgd_update(int32_t k, double *w, double *h, double a, double lambda,
+                    double s, int32_t h_uses_new_w) {
+  double dot = 0.0;
+  for (int32_t l = 0; l < k; ++l) dot += w[l] * h[l];
+  const double e = a - dot;
+  for (int32_t l = 0; l < k; ++l) {
+    const double w_old = w[l];
+    const double h_old = h[l];
+    const double w_new = w_old + s * (e * h_old - lambda * w_old);
+    const double w_for_h = h_uses_new_w ? w_new : w_old;
+    w[l] = w_new;
+    h[l] = h_old + s * (e * w_for_h - lambda * h_old);
+  }
+}
+
+/* The same update carried out entirely in binary32 (for the FP32 replay). */
+void orc_sgd_update_f32(int32_t k, float *w, float *h, float a, float lambda,
+                        float s) {
+  float dot = 0.0f;
+  for (int32_t l = 0; l < k; ++l) dot += w[l] * h[l];
+  const float e = a - dot;
+  for (int32_t l = 0; l < k; ++l) {
+    const float w_old = w[l];
+    const float h_old = h[l];
+    w[l] = w_old + s * (e * h_old - lambda * w_old);
+    h[l] = h_old + s * (e * w_old - lambda * h_old);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Objective J(W,H), simplified form of Eq. obj_fcn (Sec. 2):               */
+/*   J = 1/2 sum_{(i,j) in Omega} [ (A_ij - <w_i,h_j>)^2                    */
+/*                                  + lambda (|w_i|^2 + |h_j|^2) ]          */
+/* ------------------------------------------------------------------------ */
+double orc_objective(int64_t nnz, const int32_t *rows, const int32_t *cols,
+                     const double *vals, int32_t k, double lambda,
+                     const double *W, const double *H) {
+  double total = 0.0;
+  for (int64_t r = 0; r < nnz; ++r) {
+    const double *w = W + (int64_t)rows[r] * k;
+    const double *h = H + (int64_t)cols[r] * k;
+    double dot = 0.0, ww = 0.0, hh = 0.0;
+    for (int32_t l = 0; l < k; ++l) {
+      dot += w[l] * h[l];
+      ww += w[l] * w[l];
+      hh += h[l] * h[l];
+    }
+    const double e = vals[r] - dot;
+    total += e * e + lambda * (ww + hh);
+  }
+  return 0.5 * total;
+}
+
+/* Test RMSE (Sec. 5.1): sqrt( sum_test (A_ij - <w_i,h_j>)^2 / |Omega_test| ).
+ * Returns the sum of squares; the caller divides and takes the root so that
+ * an empty test set is handled where the count is known. */
+double orc_sq_error_sum(int64_t nnz, const int32_t *rows, const int32_t *cols,
+                        const double *vals, int32_t k, const double *W,
+                        const double *H) {
+  double total = 0.0;
+  for (int64_t r = 0; r < nnz; ++r) {
+    const double *w = W + (int64_t)rows[r] * k;
+    const double *h = H + (int64_t)cols[r] * k;
+    double dot = 0.0;
+    for (int32_t l = 0; l < k; ++l) dot += w[l] * h[l];
+    const double e = vals[r] - dot;
+    total += e * e;
+  }
+  return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Replay of a given serial order of token visits (Sec. 3.1: processing     */
+/* item j at worker q runs the SGD updates on Omega-bar_j^(q); Alg. 1, the  */
+/* loop over Omega-bar_j^(q)).                                              */
+/*                                                                          */
+/* visit_seg[v] names the segment Omega-bar_j^(q) processed by visit v.     */
+/* Segment s holds records seg_ptr[s] .. seg_ptr[s+1]-1, whose rows are     */
+/* rec_row and values rec_val; its item is seg_col[s].  Within a visit the  */
+/* records are applied in storage order.  rec_count[r] is the number of     */
+/* updates already applied to record r (reading R4); it is advanced here.   */
+/* W is m x k and H is n x k, row-major with pitch k.                       */
+/* Returns 0, or -1 if a segment index is out of range.                     */
+/* ------------------------------------------------------------------------ */
+int32_t orc_replay_f64(int32_t k, double lambda, double alpha, double beta,
+                       int64_t n_visits, const int64_t *visit_seg,
+                       int64_t n_seg, const int64_t *seg_ptr,
+                       const int32_t *seg_col, const int32_t *rec_row,
+                       const double *rec_val, double *W, double *H,
+                       int32_t *rec_count, int32_t h_uses_new_w) {
+  for (int64_t v = 0; v < n_visits; ++v) {
+    const int64_t s = visit_seg[v];
+    if (s < 0 || s >= n_seg) return -1;
+    double *h = H + (int64_t)seg_col[s] * k;
+    for (int64_t r = seg_ptr[s]; r < seg_ptr[s + 1]; ++r) {
+      double *w = W + (int64_t)rec_row[r] * k;
+      const double step = orc_step_size(alpha, beta, rec_count[r]);
+      orc_sgd_update(k, w, h, rec_val[r], lambda, step, h_uses_new_w);
+      rec_count[r] += 1;
+    }
+  }
+  return 0;
+}
+
+/* The same replay with W, H and all arithmetic in binary32; the step size is
+ * evaluated in binary64 and rounded once. */
+int32_t orc_replay_f32(int32_t k, float lambda, double alpha, double beta,
+                       int64_t n_visits, const int64_t *visit_seg,
+                       int64_t n_seg, const int64_t *seg_ptr,
+                       const int32_t *seg_col, const int32_t *rec_row,
+                       const float *rec_val, float *W, float *H,
+                       int32_t *rec_count) {
+  for (int64_t v = 0; v < n_visits; ++v) {
+    const int64_t s = visit_seg[v];
+    if (s < 0 || s >= n_seg) return -1;
+    float *h = H + (int64_t)seg_col[s] * k;
+    for (int64_t r = seg_ptr[s]; r < seg_ptr[s + 1]; ++r) {
+      float *w = W + (int64_t)rec_row[r] * k;
+      const float step = (float)orc_step_size(alpha, beta, rec_count[r]);
+      orc_sgd_update_f32(k, w, h, rec_val[r], lambda, step);
+      rec_count[r] += 1;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Serial simulation of NOMAD (Alg. 1) with p simulated worker queues.      */
+/*                                                                          */
+/* mode 0 ("epoch", permutation circulation of Sec. 3.4): in every epoch    */
+/*   item j visits each worker that holds ratings of j exactly once, in a   */
+/*   fresh uniformly random order (Fisher-Yates on the list of its          */
+/*   segments, stream (seed; j, epoch, 0, 0x4f524331)).  Its first queue is */
+/*   the first worker of epoch 0's order (Alg. 1 places every item in a     */
+/*   random queue).  The run ends when every item has finished n_epochs.    */
+/* mode 1 ("uniform", Alg. 1 literally): the first queue and every next     */
+/*   queue are uniform over all p workers (streams (seed; j, hop, 1, tag)), */
+/*   a visit to a worker without ratings of j does nothing, and the run     */
+/*   stops once n_epochs * nnz updates have been applied.                   */
+/*                                                                          */
+/* Workers are served round-robin q = 0,1,...,p-1, each popping at most one */
+/* item per round from the front of its FIFO queue; an empty queue is       */
+/* skipped.  The order of segments of item j is col_segs[col_seg_ptr[j] ..],*/
+/* and seg_worker[s] is the worker of segment s.  Visits are appended to    */
+/* visit_log (segment index, or -1 for an empty uniform-mode visit) when    */
+/* visit_log is not NULL and there is room (log_cap).                       */
+/* Returns the number of visits, or -1 on a bad argument.                   */
+/* ------------------------------------------------------------------------ */
+int64_t orc_serial_nomad(int32_t k, double lambda, double alpha, double beta,
+                         int32_t p, int64_t n, int64_t n_seg,
+                         const int64_t *seg_ptr, const int32_t *seg_col,
+                         const int32_t *seg_worker, const int32_t *rec_row,
+                         const double *rec_val, const int64_t *col_seg_ptr,
+                         const int64_t *col_segs, int32_t n_epochs,
+                         uint64_t seed, int32_t mode, double *W, double *H,
+                         int32_t *rec_count, int64_t *visit_log,
+                         int64_t log_cap) {
+  if (p <= 0 || n < 0 || (mode != 0 && mode != 1)) return -1;
+  const uint32_t TAG = 0x4f524331u;
+  /* FIFO queue per worker, each able to hold all n items. */
+  int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(p * (n + 1)));
+  int64_t *qhead = (int64_t *)calloc((size_t)p, sizeof(int64_t));
+  int64_t *qlen = (int64_t *)calloc((size_t)p, sizeof(int64_t));
+  int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_seg + 1));
+  int64_t *hop = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+  int32_t *epoch = (int32_t *)calloc((size_t)(n + 1), sizeof(int32_t));
+  if (!queue || !qhead || !qlen || !order || !hop || !epoch) {
+    free(queue); free(qhead); free(qlen); free(order); free(hop); free(epoch);
+    return -1;
+  }
+  int64_t total_nnz = seg_ptr[n_seg];
+  int64_t n_visits = 0, n_updates = 0;
+
+#define PUSH(q, j)                                                    \
+  do {                                                                \
+    int64_t pos_ = (qhead[(q)] + qlen[(q)]) % (n + 1);                \
+    queue[(int64_t)(q) * (n + 1) + pos_] = (j);                       \
+    qlen[(q)] += 1;                                                   \
+  } while (0)
+
+  /* A fresh uniformly random order of item j's segments for epoch e. */
+#define SHUFFLE(j, e)                                                       \
+  do {                                                                      \
+    int64_t b_ = col_seg_ptr[(j)], d_ = col_seg_ptr[(j) + 1] - b_;          \
+    for (int64_t t_ = 0; t_ < d_; ++t_) order[b_ + t_] = col_segs[b_ + t_]; \
+    for (int64_t t_ = d_ - 1; t_ > 0; --t_) {                               \
+      uint32_t wd_ = rand_word(seed, (uint32_t)(j), (uint32_t)(e),          \
+                               (uint32_t)t_, TAG, 0);                       \
+      int64_t u_ = (int64_t)bounded(wd_, (uint32_t)(t_ + 1));               \
+      int64_t tmp_ = order[b_ + t_];                                        \
+      order[b_ + t_] = order[b_ + u_];                                      \
+      order[b_ + u_] = tmp_;                                                \
+    }                                                                       \
+  } while (0)
+
+  /* Initial queues (Alg. 1 "initialize queues"). */
+  for (int64_t j = 0; j < n; ++j) {
+    if (mode == 0) {
+      if (col_seg_ptr[j + 1] == col_seg_ptr[j] || n_epochs <= 0) continue;
+      SHUFFLE(j, 0);
+      PUSH(seg_worker[order[col_seg_ptr[j]]], j);
+    } else {
+      uint32_t wd = rand_word(seed, (uint32_t)j, 0u, 1u, TAG, 1);
+      PUSH((int32_t)bounded(wd, (uint32_t)p), j);
+    }
+  }
+
+  const int64_t budget = (int64_t)n_epochs * total_nnz;
+  int busy = 1;
+  while (busy) {
+    busy = 0;
+    for (int32_t q = 0; q < p; ++q) {
+      if (qlen[q] == 0) continue;
+      if (mode == 1 && n_updates >= budget) break;
+      busy = 1;
+      int64_t j = queue[(int64_t)q * (n + 1) + qhead[q]];
+      qhead[q] = (qhead[q] + 1) % (n + 1);
+      qlen[q] -= 1;
+      /* Find segment (q, j): linear search over item j's segments. */
+      int64_t seg = -1;
+      for (int64_t t = col_seg_ptr[j]; t < col_seg_ptr[j + 1]; ++t)
+        if (seg_worker[col_segs[t]] == q) { seg = col_segs[t]; break; }
+      if (visit_log && n_visits < log_cap) visit_log[n_visits] = seg;
+      n_visits += 1;
+      if (seg >= 0 && seg_col[seg] != j) seg = -2; /* corrupt layout */
+      if (seg == -2) break;
+      if (seg >= 0) {
+        double *h = H + j * (int64_t)k;
+        for (int64_t r = seg_ptr[seg]; r < seg_ptr[seg + 1]; ++r) {
+          double *w = W + (int64_t)rec_row[r] * k;
+          double step = orc_step_size(alpha, beta, rec_count[r]);
+          orc_sgd_update(k, w, h, rec_val[r], lambda, step, 0);
+          rec_count[r] += 1;
+          n_updates += 1;
+        }
+      }
+      if (mode == 0) {
+        int64_t d = col_seg_ptr[j + 1] - col_seg_ptr[j];
+        hop[j] += 1;
+        if (hop[j] == d) {
+          hop[j] = 0;
+          epoch[j] += 1;
+          if (epoch[j] >= n_epochs) continue; /* item j is finished */
+          SHUFFLE(j, epoch[j]);
+        }
+        PUSH(seg_worker[order[col_seg_ptr[j] + hop[j]]], j);
+      } else {
+        hop[j] += 1;
+        uint32_t wd = rand_word(seed, (uint32_t)j, (uint32_t)hop[j], 1u, TAG, 1);
+        PUSH((int32_t)bounded(wd, (uint32_t)p), j);
+      }
+    }
+    if (mode == 1 && n_updates >= budget) break;
+  }
+#undef PUSH
+#undef SHUFFLE
+  free(queue); free(qhead); free(qlen); free(order); free(hop); free(epoch);
+  return n_visits;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Textbook SGD (Sec. 2.3): each epoch visits every rating once in a fresh  */
+/* uniformly random order (Fisher-Yates, stream (seed; t, epoch, 2, tag)).  */
+/* Step size from the per-rating update count (reading R4).                 */
+/* ------------------------------------------------------------------------ */
+int32_t orc_shuffled_sgd(int32_t k, double lambda, double alpha, double beta,
+                         int64_t nnz, const int32_t *rows, const int32_t *cols,
+                         const double *vals, int32_t n_epochs, uint64_t seed,
+                         double *W, double *H, int32_t *rec_count) {
+  const uint32_t TAG = 0x4f524332u;
+  int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz + 1));
+  if (!perm) return -1;
+  for (int32_t e = 0; e < n_epochs; ++e) {
+    for (int64_t r = 0; r < nnz; ++r) perm[r] = r;
+    for (int64_t t = nnz - 1; t > 0; --t) {
+      uint32_t wd = rand_word(seed, (uint32_t)t, (uint32_t)e,
+                              (uint32_t)((uint64_t)t >> 32), TAG, 2);
+      int64_t u = (int64_t)bounded(wd, (uint32_t)(t + 1));
+      int64_t tmp = perm[t];
+      perm[t] = perm[u];
+      perm[u] = tmp;
+    }
+    for (int64_t v = 0; v < nnz; ++v) {
+      int64_t r = perm[v];
+      double *w = W + (int64_t)rows[r] * k;
+      double *h = H + (int64_t)cols[r] * k;
+      double step = orc_step_size(alpha, beta, rec_count[r]);
+      orc_sgd_update(k, w, h, vals[r], lambda, step, 0);
+      rec_count[r] += 1;
+    }
+  }
+  free(perm);
+  return 0;
+}
