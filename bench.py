@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the NOMAD SGD hot path on GB300.
+
+One step = one NOMAD epoch over the whole training set (every rating updated
+once, through the persistent kernel: token queues, routing, fused SGD step)
+followed by the test-RMSE reduction, on the Netflix-shaped synthetic
+workload (m=480,189, n=17,770, ~100.5M train + ~1.4M test ratings, k=100,
+lambda=0.05, Table 1's alpha=0.012, beta=0.05).  The ratings and factors
+(about 1.2 GB) are larger than the 129 MB L2, so no flush is needed between
+steps.
+
+value  = rating updates per second over the timed steps, whole job (sum of
+         the ranks' updates / max over ranks of the timed span).
+e2e    = the same metric through the C ABI with host buffers: every step
+         loads the ratings from pinned host memory (H2D + device layout
+         build), runs one epoch, and evaluates the test RMSE from pinned host
+         arrays (H2D, result D2H).
+roofline = algorithmic HBM bytes of the epoch kernel (per update: w_i read +
+         write, 2*k*4 bytes, plus the 8-byte rating record; h_j stays
+         on-chip) / its CUDA-event duration, against the measured copy
+         bandwidth.
+cpu_baseline = the serial CPU oracle (binary64 shuffled SGD, one thread) on
+         a bounded sample of the same workload.
+
+Several GPUs (torchrun): the path does not shard (one problem per GPU), so
+every rank runs an independent replica.  --impl reference times the CPU
+oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("SGD rating-updates/sec and time-to-target test RMSE, 1×GB300, "
+          "% HBM roofline")
+UNIT = "updates/s"
+
+CONFIGS = {
+    # name: (generator, k, lambda, alpha, beta)
+    "netflix": ("netflix_shaped", 100, 0.05, 0.012, 0.05),
+    "yahoo": ("yahoo_shaped", 100, 1.0, 0.00075, 0.01),
+    "hugewiki": ("hugewiki_shaped", 100, 0.01, 0.001, 0.0),
+    "tiny": ("tiny_planted", 10, 0.05, 0.012, 0.05),
+}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.file is None or self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.file.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max_sum(t_local: float, units_local: float, world: int, device=None):
+    """(max over ranks of t_local, sum over ranks of units_local)."""
+    if world == 1:
+        return t_local, units_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- workloads
+def make_workload(cfg: str, device):
+    import synth
+    gen, k, lam, alpha, beta = CONFIGS[cfg]
+    fn = getattr(synth, gen)
+    r = fn(device=device) if cfg == "tiny" else fn(1.0, device=device)
+    return r, k, lam, alpha, beta
+
+
+def workload_name(r, k):
+    return "%s m=%d n=%d train=%d test=%d k=%d" % (
+        r.name, r.m, r.n, r.nnz, int(r.test_rows.numel()), k)
+
+
+def cpu_sample_run(r, k, lam, alpha, beta, target_updates: int, seed: int = 5):
+    """The CPU oracle (binary64 shuffled SGD, one thread) for one epoch over a
+    sample of the workload: the ratings of every `stride`-th user.  Returns
+    (updates, seconds, description)."""
+    import numpy as np
+    import oracle
+    rows = r.train_rows.cpu().numpy()
+    cols = r.train_cols.cpu().numpy()
+    vals = r.train_vals.cpu().numpy()
+    stride = max(1, int(round(rows.size / max(target_updates, 1))))
+    sel = (rows % stride) == 0
+    rs, cs, vs = rows[sel], cols[sel], vals[sel]
+    W = oracle.init_factor(r.m, k, 1, 0)
+    H = oracle.init_factor(r.n, k, 1, 1)
+    t0 = time.perf_counter()
+    oracle.shuffled_sgd(rs, cs, vs, W, H, lam, alpha, beta, 1, seed)
+    dt = time.perf_counter() - t0
+    desc = ("one epoch of binary64 shuffled SGD over the ratings of every %d-th user "
+            "(%d of %d ratings), k=%d" % (stride, rs.size, rows.size, k))
+    return int(rs.size), dt, desc
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1312_0193_gb300 import Nomad
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    r, k, lam, alpha, beta = make_workload(args.config, dev)
+    nnz = r.nnz
+    nm = Nomad(r.m, r.n, k, lam, alpha=alpha, beta=beta, device=local,
+               n_workers=args.workers, warps_per_block=args.warps_per_block,
+               precision=args.precision)
+    stream = torch.cuda.current_stream(dev)
+    t_load0 = time.perf_counter()
+    nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
+    load_s = time.perf_counter() - t_load0
+    info = nm.info()
+    te_r, te_c, te_v = r.test_rows, r.test_cols, r.test_vals
+
+    def step():
+        nm.epoch(1)
+        return nm.rmse(te_r, te_c, te_v)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    launches0 = nm.info()["kernel_launches"]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kernel_ms = []
+    rmses = []
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            nm.epoch(1)
+            rmses.append(nm.rmse(te_r, te_c, te_v))
+            kernel_ms.append(nm.last_epoch_kernel_ms())
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    t_local = ev0.elapsed_time(ev1) / 1000.0
+    launches = nm.info()["kernel_launches"] - launches0
+    t_max, units = reduce_max_sum(t_local, float(nnz) * args.steps, world, dev)
+    value = units / t_max
+
+    # end to end through the C ABI with pinned host buffers
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    h_rows = r.train_rows.cpu().pin_memory()
+    h_cols = r.train_cols.cpu().pin_memory()
+    h_vals = r.train_vals.cpu().pin_memory()
+    h_te = [t.cpu().pin_memory() for t in (te_r, te_c, te_v)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        nm.load_coo(h_rows, h_cols, h_vals)
+        nm.epoch(1)
+        nm.rmse(*h_te)
+    torch.cuda.synchronize(dev)
+    e2e_local = time.perf_counter() - t0
+    e2e_t, e2e_units = reduce_max_sum(e2e_local, float(nnz) * e2e_steps, world, dev)
+    h2d = 12 * nnz + 12 * int(te_r.numel())
+
+    bytes_per_update = 2 * k * 4 + 8
+    kern_avg_s = statistics.mean(kernel_ms) / 1000.0
+    achieved_gbs = nnz * bytes_per_update / kern_avg_s / 1e9
+    peak, peak_src = load_peaks()
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "epoch_kernel_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                tj = json.load(f)
+            if tj.get("config") == args.config and tj.get("kernel_rev") == kernel_rev():
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        upd, secs, desc = cpu_sample_run(r, k, lam, alpha, beta, args.cpu_sample)
+        cpu = {"value": upd / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": desc, "seconds": round(secs, 2)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max * 1000.0 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "bf16-storage/f32",
+            "data": "synthetic (seeded; stands in for the paper's dataset)",
+            "config": {
+                "workload": workload_name(r, k), "lambda": lam, "alpha": alpha,
+                "beta": beta, "mode": "epoch (permutation circulation)",
+                "workers": info["p"], "warps_per_block": info["warps_per_block"],
+                "segments": info["n_segments"],
+                "ratings_per_visit": round(nnz / max(info["n_segments"], 1), 3),
+                "step": "one epoch (all ratings) + test RMSE",
+                "l2": "inputs larger than L2 (ratings %.0f MB, W %.0f MB); no flush" % (
+                    nnz * 8 / 1e6, r.m * info["pitch"] * 4 / 1e6),
+                "parallelism": "replicas x%d (one independent problem per GPU)" % world,
+                "load_seconds_first": round(load_s, 3),
+            },
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
+                         "unit": "GB/s", "frac": achieved_gbs / peak, "traffic": traffic,
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
+                         if peak_src == "measured" else "fallback 6.8 TB/s",
+                         "kernel": "nomad_epoch_kernel", "kernel_ms": kern_avg_s * 1e3,
+                         "bytes_per_update": bytes_per_update},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_units / e2e_t, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
+                    "steps": e2e_steps,
+                    "step": "load_ratings(pinned host COO) + epoch + rmse(pinned host)"},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "test_rmse_last": rmses[-1] if rmses else None,
+        }
+        print(json.dumps(out), flush=True)
+    nm.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def kernel_rev():
+    """Hash of the epoch kernel's source, to tie profile figures to code."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1312_0193_gb300", "csrc", "sgd.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle as it stands, on the host cores, rank 0 only."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    dev = torch.device("cuda", local) if torch.cuda.is_available() else "cpu"
+    r, k, lam, alpha, beta = make_workload(args.config, dev)
+    per_step = max(1, args.ref_sample)
+    for _ in range(args.warmup):
+        cpu_sample_run(r, k, lam, alpha, beta, per_step // 4)
+    tot_u, tot_t, desc = 0, 0.0, ""
+    for s in range(args.steps):
+        u, t, desc = cpu_sample_run(r, k, lam, alpha, beta, per_step, seed=11 + s)
+        tot_u += u
+        tot_t += t
+    v = tot_u / tot_t
+    out = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_t * 1000.0 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded; stands in for the paper's dataset)",
+        "config": {"workload": workload_name(r, k), "lambda": lam, "alpha": alpha,
+                   "beta": beta},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="netflix")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--workers", type=int, default=0)
+    ap.add_argument("--warps-per-block", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=25_000_000,
+                    help="ratings in the CPU-oracle baseline sample")
+    ap.add_argument("--ref-sample", type=int, default=2_000_000,
+                    help="ratings per step of the reference arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * nomad.h -- C ABI of libnomad, a GB300 (sm_103a) implementation of the SGD
+ * hot path of NOMAD (Yun, Yu, Hsieh, Vishwanathan, Dhillon, "NOMAD:
+ * Non-locking, stOchastic Multi-machine algorithm for Asynchronous and
+ * Decentralized matrix completion", arXiv 1312.0193).
+ *
+ * The library learns W (m x k) and H (n x k) with A ~ W H^T over the observed
+ * ratings Omega (Sec. 2) by per-rating SGD (Sec. 2.3) under NOMAD's ownership
+ * passing schedule (Sec. 3.1, Alg. 1): users are split into p row blocks,
+ * each owned by one worker (one warp of a persistent kernel); each item
+ * vector h_j is a token owned by exactly one worker at a time and handed
+ * between workers through device-resident queues.
+ *
+ * Conventions for every entry point:
+ *  - Indices are 0-based int32; m, n < 2^31; nnz < 2^32.
+ *  - Pointers are plain host or device addresses, as the `device_ptrs`
+ *    argument says (1 = device memory of the handle's device, 0 = host
+ *    memory, pinned or pageable).  The library copies what it needs; the
+ *    caller keeps ownership of its buffers and may reuse them on return
+ *    (for device inputs: once the work queued on `stream` has passed).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated.
+ *  - The handle owns all device memory it allocates (cudaMalloc) and frees it
+ *    in nomad_destroy.  A handle is not thread-safe: one host thread at a
+ *    time.
+ *  - Return value: NOMAD_OK (0) or a negative NOMAD_ERR_* code; the text of
+ *    the last error of a handle is available from nomad_last_error_message.
+ */
+#ifndef NOMAD_H_
+#define NOMAD_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NOMAD_API __attribute__((visibility("default")))
+#else
+#define NOMAD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+#define NOMAD_OK 0
+#define NOMAD_ERR_INVALID_ARG (-1) /* bad size, pointer, mode or order of calls */
+#define NOMAD_ERR_OOM (-2)         /* device or host allocation failed */
+#define NOMAD_ERR_DUP_ENTRY (-3)   /* a pair (i,j) occurs twice: Omega is a set (Sec. 2) */
+#define NOMAD_ERR_TIMEOUT (-4)     /* a worker waited longer than spin_timeout_ns for a token */
+#define NOMAD_ERR_OWNERSHIP (-5)   /* debug check: an item token held by two workers */
+#define NOMAD_ERR_CUDA (-6)        /* a CUDA runtime call failed */
+#define NOMAD_ERR_RANGE (-7)       /* an index is outside [0,m) or [0,n) */
+#define NOMAD_ERR_UNSUPPORTED (-8) /* shape or option this build does not handle */
+#define NOMAD_ERR_STATE (-9)       /* e.g. nomad_epoch before nomad_load_ratings */
+
+/* ---------------------------------------------------------------- options */
+/* Routing of an item token after a visit (Sec. 3.1 / Alg. 1 / Sec. 3.4). */
+#define NOMAD_MODE_EPOCH 0   /* permutation circulation: in every epoch item j
+                                visits each worker that holds ratings of j
+                                exactly once, in a fresh pseudo-random order
+                                (Sec. 3.4); t of Eq. stepsize_method is the
+                                epoch index */
+#define NOMAD_MODE_UNIFORM 1 /* Alg. 1 literally: the next worker is uniform
+                                over all p workers; a per-rating counter gives
+                                t; one "epoch" is |Omega| updates */
+
+#define NOMAD_FP32 0 /* W, H stored in binary32 */
+#define NOMAD_BF16 1 /* W, H stored in bfloat16, FP32 arithmetic, stochastic
+                        rounding on write-back */
+
+#define NOMAD_PARTITION_RATINGS 0 /* blocks with equal numbers of ratings
+                                     (footnote of Sec. 3.1) */
+#define NOMAD_PARTITION_USERS 1   /* blocks with equal numbers of users
+                                     (Sec. 3.1) */
+
+#define NOMAD_COO 0 /* rating input as (row, col, value) triples */
+#define NOMAD_CSC 1 /* rating input as column pointers + row indices */
+
+/* Schedule and hyper-parameters.  Fill with nomad_schedule_default first. */
+typedef struct nomad_schedule {
+  float alpha;      /* step size s_t = alpha / (1 + beta t^1.5), Sec. 5.1 */
+  float beta;       /* Eq. stepsize_method; Table 1 gives (alpha, beta) */
+  int32_t mode;     /* NOMAD_MODE_* */
+  int32_t precision;/* NOMAD_FP32 or NOMAD_BF16 */
+  int32_t partition;/* NOMAD_PARTITION_* */
+  int32_t n_workers;/* p; 0 = every warp the persistent kernel can keep
+                       resident on the device */
+  int32_t warps_per_block; /* 0 = library default */
+  int32_t debug;    /* 1 = record the serial visit order (replay log),
+                       per-rating update counts and item-ownership checks */
+  uint64_t seed;    /* factor initialisation, routing and rounding draws */
+  int64_t spin_timeout_ns; /* a worker that waits longer than this for a
+                       token stops and nomad_epoch reports NOMAD_ERR_TIMEOUT;
+                       0 = 10 s */
+  int32_t device;   /* CUDA device ordinal */
+  int32_t debug_drop_item; /* testing only: item id whose token is never
+                       handed to a worker in nomad_epoch (a planted lost
+                       message); -1 = none */
+  int64_t reserved[6];
+} nomad_schedule;
+
+typedef struct nomad_handle nomad_t;
+
+/* Facts about a handle (sizes of the layout built by nomad_load_ratings). */
+typedef struct nomad_info {
+  int64_t m, n;
+  int32_t k;
+  int32_t p;               /* number of workers (row blocks) */
+  int64_t nnz;             /* training ratings loaded */
+  int64_t n_segments;      /* non-empty sets Omega-bar_j^(q) (Sec. 3.1) */
+  int64_t epochs_done;     /* epochs completed since load / set_factors */
+  int32_t pitch;           /* row pitch of W and H on the device, elements */
+  int32_t precision;
+  int32_t mode;
+  int32_t warps_per_block;
+  int32_t blocks;          /* persistent grid size */
+  int32_t sm_count;
+  int64_t device_bytes;    /* device memory held by the handle */
+  int64_t kernel_launches; /* kernels launched by the handle so far */
+  int64_t reserved[3];
+} nomad_info;
+
+/* Library defaults: alpha 0.012, beta 0.05 (Table 1, Netflix), epoch mode,
+ * FP32, ratings-balanced partition, automatic p, seed 1, 10 s timeout. */
+NOMAD_API void nomad_schedule_default(nomad_schedule *s);
+
+/* Create a problem with m users, n items, rank k and regularisation lambda
+ * (Eq. obj_fcn).  Allocates and initialises W and H with independent
+ * UniformReal(0, 1/sqrt(k)) entries (Alg. 1, Sec. 5.1).  1 <= k <= 512.
+ * On success *out is a new handle; on failure *out is NULL. */
+NOMAD_API int nomad_create(int64_t m, int64_t n, int32_t k, float lambda,
+                 const nomad_schedule *s, nomad_t **out);
+
+/* Load the training ratings and build the layout of Sec. 3.1: rows split
+ * into p blocks I_q, and for every worker q the sets Omega-bar_j^(q) of its
+ * ratings of item j, stored as a compressed per-worker CSC (only non-empty
+ * columns), rows ascending inside a set.  The data are never moved again.
+ *  fmt NOMAD_COO: major = const int32_t rows[nnz], minor = cols[nnz].
+ *  fmt NOMAD_CSC: major = const int64_t colptr[n+1], minor = rows[nnz].
+ *  vals = const float[nnz].
+ * Errors: NOMAD_ERR_RANGE (index out of range), NOMAD_ERR_DUP_ENTRY.
+ * Synchronises with the device before returning.  May be called again to
+ * replace the ratings (the factors are kept). */
+NOMAD_API int nomad_load_ratings(nomad_t *h, int32_t fmt, int64_t nnz, const void *major,
+                       const int32_t *minor, const float *vals,
+                       int32_t device_ptrs, void *stream);
+
+/* Run n_epochs epochs of NOMAD (Alg. 1) in one persistent launch: every
+ * worker pops item tokens from its queue, applies the SGD updates of
+ * Eq. w_update / h_update to its ratings of that item, and hands the token
+ * on.  In NOMAD_MODE_EPOCH every rating is updated exactly once per epoch.
+ * Asynchronous on `stream`; errors raised on the device (timeout, ownership)
+ * are reported by the next nomad_check / nomad_rmse / nomad_objective /
+ * nomad_get_factors call. */
+NOMAD_API int nomad_epoch(nomad_t *h, int32_t n_epochs, void *stream);
+
+/* Wait for the handle's work on `stream` and report any device-side error
+ * of earlier nomad_epoch calls (then clears it). */
+NOMAD_API int nomad_check(nomad_t *h, void *stream);
+
+/* Test RMSE (Sec. 5.1) over nnz ratings: sqrt(sum (A_ij - <w_i,h_j>)^2 /
+ * nnz).  Products and residuals in binary32, sums in binary64.  Writes the
+ * result to *out (host).  Synchronous.  nnz = 0 gives NaN. */
+NOMAD_API int nomad_rmse(nomad_t *h, int64_t nnz, const int32_t *rows,
+               const int32_t *cols, const float *vals, int32_t device_ptrs,
+               double *out, void *stream);
+
+/* Objective J(W,H) of Eq. obj_fcn over the loaded training ratings:
+ * 1/2 sum_Omega [ (A_ij - <w_i,h_j>)^2 + lambda (|w_i|^2 + |h_j|^2) ],
+ * per-rating terms in binary32, sums in binary64.  Synchronous. */
+NOMAD_API int nomad_objective(nomad_t *h, double *out, void *stream);
+
+/* Copy the factors out as dense row-major binary32 arrays W[m*k], H[n*k]
+ * (BF16 storage is widened exactly).  Either pointer may be NULL.
+ * Synchronous. */
+NOMAD_API int nomad_get_factors(nomad_t *h, float *W, float *H, int32_t device_ptrs,
+                      void *stream);
+
+/* Replace the factors (checkpoint resume); epochs_done is set to
+ * `epochs_done` so that the step-size schedule continues from there.
+ * BF16 storage rounds to nearest.  Either pointer may be NULL. Synchronous. */
+NOMAD_API int nomad_set_factors(nomad_t *h, const float *W, const float *H,
+                      int32_t device_ptrs, int64_t epochs_done, void *stream);
+
+/* Device time in milliseconds of the persistent NOMAD kernel of the last
+ * nomad_epoch call, from CUDA events recorded on that call's stream right
+ * before and after the launch.  Waits for the second event. */
+NOMAD_API int nomad_last_epoch_kernel_ms(nomad_t *h, float *ms);
+
+/* Sizes and settings of the handle. */
+NOMAD_API int nomad_get_info(const nomad_t *h, nomad_info *out);
+
+/* Host copies of the layout built by nomad_load_ratings, each pointer may be
+ * NULL: row_worker[m] (the block of every user), seg_worker[S], seg_col[S],
+ * seg_ptr[S+1] (record offsets), rec_row[nnz], rec_val[nnz] (records in
+ * segment order).  S = nomad_info.n_segments.  Synchronous. */
+NOMAD_API int nomad_get_layout(nomad_t *h, int32_t *row_worker, int32_t *seg_worker,
+                     int32_t *seg_col, int64_t *seg_ptr, int32_t *rec_row,
+                     float *rec_val);
+
+/* Debug mode only (schedule.debug = 1): the serial visit order of the last
+ * nomad_epoch call.  Visits are ordered by a ticket each worker takes right
+ * after it pops a token; that order is a valid serialisation (two visits that
+ * share an item or a worker are ordered as they happened).  seg[v] is the
+ * segment (index into the layout) and epoch[v] the epoch of visit v.  Writes
+ * min(cap, count) entries and the total count to *count.  Synchronous. */
+NOMAD_API int nomad_get_replay_log(nomad_t *h, int64_t cap, int32_t *seg, int32_t *epoch,
+                         int64_t *count);
+
+/* Debug mode only: per-record update counts since load (records in segment
+ * order) and the number of ownership violations seen.  Synchronous. */
+NOMAD_API int nomad_get_debug_counts(nomad_t *h, int32_t *rec_count,
+                           int64_t *ownership_violations);
+
+/* Free every resource of the handle (NULL is ignored). */
+NOMAD_API void nomad_destroy(nomad_t *h);
+
+/* Static text for an error code. */
+NOMAD_API const char *nomad_error_string(int32_t code);
+
+/* Text of the last error of the handle ("" if none). */
+NOMAD_API const char *nomad_last_error_message(const nomad_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NOMAD_H_ */

@@ -1,0 +1,220 @@
+// nomad_internal.cuh -- internal declarations of libnomad (GB300 / sm_103a).
+//
+// Device-side building blocks shared by the translation units of the CUDA
+// path: the counter-based generator, memory-order primitives written as
+// inline PTX, the parameter blocks of the kernels and the handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "nomad.h"
+
+namespace nomad {
+
+// ---------------------------------------------------------------- generator
+// Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11): ten
+// rounds of two 32x32->64 multiplies, the key advanced by the Weyl constants
+// between rounds.
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+#if defined(__CUDA_ARCH__)
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#else
+    const uint64_t p0 = 0xD2511F53ull * c.x, p1 = 0xCD9E8D57ull * c.z;
+    const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
+    const uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+#endif
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Stream tags: the fourth counter word separates the uses of the generator.
+constexpr uint32_t kTagInitW = 0u;       // W entries (factor 0)
+constexpr uint32_t kTagInitH = 1u;       // H entries (factor 1)
+constexpr uint32_t kTagItinerary = 0x49544e52u;  // epoch-mode visit orders
+constexpr uint32_t kTagUniform = 0x554e4946u;    // uniform-mode routing
+constexpr uint32_t kTagRounding = 0x53524e44u;   // stochastic rounding
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned long long ld_acquire_u64(
+    const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p,
+                                               unsigned long long v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------- kernels
+// Status words written by device code: [0] error code (0 = ok), [1] worker,
+// [2] detail, [3] count of ownership violations (debug).
+constexpr int kStatusWords = 4;
+
+struct SgdParams {
+  void* W;                  // m x pitch (fp32 or bf16)
+  void* H;                  // n x pitch
+  int32_t pitch;            // elements per row
+  int32_t k4;               // 4-element chunks holding the k entries
+  const int2* rec;          // {row, value bits} in segment order
+  const int64_t* seg_ptr;   // S+1
+  const int32_t* seg_col;   // S
+  const int32_t* seg_worker;// S
+  const int32_t* worker_seg_ptr;  // p+1
+  const int32_t* col_seg_ptr;     // n+1
+  const int32_t* col_segs;        // S: segments of each item, by worker
+  unsigned long long* ring; // lap-tagged slots {lap:32 | segment:32}
+  const int64_t* ring_base; // p
+  const int32_t* ring_log2; // p: log2 of the ring capacity
+  uint32_t* ring_tail;      // p: producer reservation counters
+  int32_t* tok_hop;         // n: hop within the current epoch
+  int32_t* tok_epoch;       // n: absolute epoch of the token
+  const float* step;        // n_epochs step sizes (epoch mode)
+  int32_t epoch0;
+  int32_t n_epochs;
+  int32_t p;
+  float lambda;
+  float alpha, beta;        // uniform mode computes s_t on the fly
+  uint32_t seed_lo, seed_hi;
+  int64_t timeout_ns;
+  int32_t* status;
+  // uniform mode
+  unsigned long long* upd_done;
+  unsigned long long upd_budget;
+  int32_t* stop;
+  // debug mode
+  uint32_t* log_ticket;
+  int32_t* log_seg;
+  int32_t* log_epoch;
+  int64_t log_cap;
+  int32_t* owner;
+  int32_t* rec_count;
+  int32_t drop_item;
+};
+
+struct EvalParams {
+  const void* W;
+  const void* H;
+  int32_t pitch;
+  int32_t k4;
+};
+
+// ---------------------------------------------------------------- handle
+struct DeviceBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace nomad
+
+struct nomad_handle {
+  int64_t m = 0, n = 0;
+  int32_t k = 0, k4 = 0, pitch = 0;
+  float lambda = 0.f;
+  nomad_schedule sched{};
+  int device = 0;
+  int sm_count = 0;
+  int32_t p = 0;
+  int32_t warps_per_block = 0;
+  int32_t blocks = 0;
+  int64_t nnz = 0;
+  int64_t n_seg = 0;
+  int64_t epochs_done = 0;
+  int64_t ring_slots = 0;
+  bool loaded = false;
+  std::string last_error;
+  // factors
+  void* W = nullptr;
+  void* H = nullptr;
+  // layout
+  int32_t* row_worker = nullptr;   // m
+  int2* rec = nullptr;             // nnz
+  int64_t* seg_ptr = nullptr;      // S+1
+  int32_t* seg_col = nullptr;      // S
+  int32_t* seg_worker = nullptr;   // S
+  int32_t* worker_seg_ptr = nullptr;  // p+1
+  int32_t* col_seg_ptr = nullptr;  // n+1
+  int32_t* col_segs = nullptr;     // S
+  // queues and tokens
+  unsigned long long* ring = nullptr;
+  int64_t* ring_base = nullptr;
+  int32_t* ring_log2 = nullptr;
+  uint32_t* ring_tail = nullptr;
+  int32_t* tok_hop = nullptr;
+  int32_t* tok_epoch = nullptr;
+  float* step = nullptr;
+  int32_t step_cap = 0;
+  int32_t* status = nullptr;       // kStatusWords
+  unsigned long long* upd_done = nullptr;
+  int32_t* stop = nullptr;
+  // scratch for reductions
+  double* partials = nullptr;
+  int32_t partials_cap = 0;
+  double* result = nullptr;
+  // debug
+  uint32_t* log_ticket = nullptr;
+  int32_t* log_seg = nullptr;
+  int32_t* log_epoch = nullptr;
+  int64_t log_cap = 0;
+  int32_t* owner = nullptr;
+  int32_t* rec_count = nullptr;
+  int64_t device_bytes = 0;
+  int64_t launches = 0;            // kernels launched by this handle
+  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+  bool ev_recorded = false;
+  std::unordered_map<void*, size_t> allocs;
+};
+
+namespace nomad {
+
+// Allocation bookkeeping (nomad_api.cu).
+cudaError_t dev_alloc(nomad_handle* h, void** p, size_t bytes);
+void dev_free(nomad_handle* h, void** p);
+
+// Layout construction (layout.cu).  Builds everything nomad_load_ratings
+// needs from device COO arrays.  Returns a NOMAD_* code.
+int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
+                 const int32_t* d_cols, const float* d_vals,
+                 cudaStream_t stream);
+
+// Persistent SGD kernel launch (sgd.cu).
+int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t stream);
+int max_resident_workers(int device, int warps_per_block, int k4,
+                         int precision, int* blocks_per_sm);
+
+// Initialisation, evaluation and factor copies (eval.cu).
+int init_factors(nomad_handle* h, cudaStream_t stream);
+int rmse_sum(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
+             const int32_t* d_cols, const float* d_vals, double* out,
+             cudaStream_t stream);
+int objective_sum(nomad_handle* h, double* out, cudaStream_t stream);
+int factors_to_f32(nomad_handle* h, int which, float* d_dense,
+                   cudaStream_t stream);
+int factors_from_f32(nomad_handle* h, int which, const float* d_dense,
+                     cudaStream_t stream);
+
+}  // namespace nomad
