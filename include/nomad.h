@@ -73,6 +73,11 @@ extern "C" {
 #define NOMAD_PARTITION_USERS 1   /* blocks with equal numbers of users
                                      (Sec. 3.1) */
 
+#define NOMAD_VARIANT_BATCHED 0 /* a worker takes up to 8 ready tokens at once,
+                                   streams W rows through shared memory
+                                   (default) */
+#define NOMAD_VARIANT_SIMPLE 1  /* a worker handles one token at a time */
+
 #define NOMAD_COO 0 /* rating input as (row, col, value) triples */
 #define NOMAD_CSC 1 /* rating input as column pointers + row indices */
 
@@ -96,7 +101,9 @@ typedef struct nomad_schedule {
   int32_t debug_drop_item; /* testing only: item id whose token is never
                        handed to a worker in nomad_epoch (a planted lost
                        message); -1 = none */
-  int64_t reserved[6];
+  int32_t variant;  /* epoch-mode worker kernel: NOMAD_VARIANT_* */
+  int32_t pad0;
+  int64_t reserved[5];
 } nomad_schedule;
 
 typedef struct nomad_handle nomad_t;

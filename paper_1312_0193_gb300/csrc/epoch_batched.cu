@@ -1,0 +1,395 @@
+// epoch_batched.cu -- the batched NOMAD worker kernel (epoch mode).
+//
+// Same worker semantics as the one-token kernel of sgd.cu (one warp = one
+// worker q of Sec. 3.1, item tokens on lap-tagged rings, permutation
+// circulation of Sec. 3.4), organised so that the latency of global memory is
+// paid per batch of tokens instead of per visit:
+//
+//  1. take the ready prefix of the own ring (up to kBatch tokens) with one
+//     acquire load per lane;
+//  2. fetch every token's metadata lane-parallel (lane b = token b);
+//  3. order the visits: long visits (>= kHeavy ratings, the items whose
+//     serial chain through h_j is longest) first, then the rest;
+//  4. copy every h_j of the batch into shared memory and the rating records
+//     of the batch, as one stream of positions, into a shared circular
+//     buffer (cp.async);
+//  5. walk the stream: W rows are copied into a ring of R shared-memory
+//     slots R-1 positions ahead of the update (cp.async), so up to R-1 rows
+//     per worker are in flight; the update itself is the fused SGD step of
+//     Eq. w_update / h_update (descent sign, old w_i in the h update);
+//  6. push long visits' tokens right after their visit, the others together
+//     at the end of the batch (one fence, lane-parallel reservations).
+//
+// A row can appear in two visits of one batch (a user who rated both items).
+// Its copy for the later visit must not be taken before the earlier visit
+// has written it: when the row of the position being prefetched equals the
+// row of a position still in the prefetch window, no copy is made and the
+// update loads the row from global memory after the earlier store (same
+// thread, program order).
+#include "sgd_common.cuh"
+
+namespace nomad {
+namespace {
+
+constexpr int kBatch = 8;      // tokens taken from the ring at once
+constexpr int kRecBuf = 128;   // circular buffer of record positions
+constexpr int kRecInit = 64;   // positions loaded before the first row copy
+constexpr int kHeavy = 32;     // visits this long go first and are pushed at once
+
+template <int CPL>
+struct RowRing {
+  static constexpr int R = 16 / CPL;  // slots; R-1 rows in flight
+};
+
+// Shared memory of one warp, in float4 units: row slots, h of the batch,
+// records (int2, two per float4), and two int4 tables of batch metadata.
+template <int CPL>
+__host__ __device__ constexpr int warp_smem_f4() {
+  return RowRing<CPL>::R * CPL * 32 + kBatch * CPL * 32 + kRecBuf / 2 + 2 * kBatch;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copies the records of stream positions [p0, p0 + count) (count <= 32) into
+// the circular buffer.  meta_a[r].y is the length and meta_b[r] = {beg_lo,
+// beg_hi, token lane, stream offset} of the rank-r visit.
+__device__ __forceinline__ void load_records(int2* recs, const int2* __restrict__ rec,
+                                             const int4* meta_a, const int4* meta_b, int nb,
+                                             int p0, int count, int lane) {
+  const int p = p0 + lane;
+  if (lane < count) {
+    int64_t src = 0;
+    for (int r = 0; r < nb; ++r) {
+      const int off = meta_b[r].w;
+      if (p >= off && p < off + meta_a[r].y)
+        src = ((int64_t(meta_b[r].y) << 32) | uint32_t(meta_b[r].x)) + (p - off);
+    }
+    cp_async8(recs + (p % kRecBuf), rec + src);
+  }
+}
+
+template <int CPL, bool DEBUG>
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
+nomad_batched_kernel(const SgdParams P) {
+  constexpr int R = RowRing<CPL>::R;
+  extern __shared__ float4 smem_f4[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int q = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (q >= P.p) return;
+  float4* rows = smem_f4 + size_t(wib) * warp_smem_f4<CPL>();
+  float4* hbuf = rows + R * CPL * 32;
+  int2* recs = reinterpret_cast<int2*>(hbuf + kBatch * CPL * 32);
+  int4* meta_a = reinterpret_cast<int4*>(recs + kRecBuf);  // {j, c, e, seg}
+  int4* meta_b = meta_a + kBatch;                          // {beg_lo, beg_hi, lane, soff}
+
+  const int64_t quota = int64_t(P.worker_seg_ptr[q + 1] - P.worker_seg_ptr[q]) * P.n_epochs;
+  const int lg = P.ring_log2[q];
+  const uint32_t qmask = (1u << lg) - 1u;
+  const unsigned long long* ring_q = P.ring + P.ring_base[q];
+  float4* __restrict__ W4 = reinterpret_cast<float4*>(P.W);
+  float4* __restrict__ H4 = reinterpret_cast<float4*>(P.H);
+  const int64_t pitch4 = P.pitch >> 2;
+  const int k4 = P.k4;
+  const float lam = P.lambda;
+  const uint2 seed = make_uint2(P.seed_lo, P.seed_hi);
+  const int epoch_end = P.epoch0 + P.n_epochs;
+  const unsigned below = (1u << lane) - 1u;
+
+  uint32_t head = 0;
+  int64_t done = 0;
+  while (done < quota) {
+    // ---- 1. the ready prefix of the ring
+    const int want = quota - done < kBatch ? int(quota - done) : kBatch;
+    unsigned long long sv = 0;
+    bool ready = false;
+    if (lane < want) {
+      const uint32_t pos = head + uint32_t(lane);
+      sv = ld_acquire_u64(ring_q + (pos & qmask));
+      ready = uint32_t(sv >> 32) == (pos >> lg);
+    }
+    const unsigned rmask = __ballot_sync(kFull, ready);
+    const int nb = __ffs(~rmask) - 1;
+    if (nb <= 0) {
+      int got = 0;
+      if (lane == 0) got = pop_token(P, q, head, lg, ring_q);
+      if (__shfl_sync(kFull, got, 0) < 0) return;
+      continue;  // the slot at head is ready now; take the prefix again
+    }
+    __syncwarp();  // each lane's acquire precedes every lane's reads below
+    head += uint32_t(nb);
+    done += nb;
+    const bool mine = lane < nb;
+    const int seg = mine ? int(uint32_t(sv)) : 0;
+
+    // ---- 2. metadata of token `lane`
+    int j = 0, c = 0;
+    int64_t beg = 0;
+    if (mine) {
+      j = __ldg(P.seg_col + seg);
+      beg = __ldg(P.seg_ptr + seg);
+      c = int(__ldg(P.seg_ptr + seg + 1) - beg);
+    }
+    int e = 0, hop = 0, cb = 0, cend = 0;
+    if (mine) {
+      e = __ldcg(P.tok_epoch + j);
+      hop = __ldcg(P.tok_hop + j);
+      cb = __ldg(P.col_seg_ptr + j);
+      cend = __ldg(P.col_seg_ptr + j + 1);
+    }
+
+    // ---- 3. processing order: long visits first, then ring order
+    const unsigned hv = __ballot_sync(kFull, mine && c >= kHeavy);
+    const unsigned lt = ((1u << nb) - 1u) & ~hv;
+    int rank = 0;
+    if (mine) rank = ((hv >> lane) & 1u) ? __popc(hv & below) : __popc(hv) + __popc(lt & below);
+    if (mine) {
+      meta_a[rank] = make_int4(j, c, 0, seg);
+      meta_b[rank] = make_int4(int(uint32_t(beg)), int(uint32_t(uint64_t(beg) >> 32)), lane, 0);
+    }
+    __syncwarp();
+    int T;
+    {  // stream offsets: exclusive prefix of the lengths in processing order
+      const int cr = lane < nb ? meta_a[lane].y : 0;
+      int incl = cr;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      T = __shfl_sync(kFull, incl, 31);
+      if (lane < nb) meta_b[lane].w = incl - cr;
+    }
+    __syncwarp();
+
+    // ---- 4. h of every token and the first records of the stream
+    for (int r = 0; r < nb; ++r) {
+      const int64_t jr = meta_a[r].x;
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int idx = lane + 32 * cc;
+        if (idx < k4) cp_async16(hbuf + (r * CPL + cc) * 32 + lane, H4 + jr * pitch4 + idx);
+      }
+    }
+    int loaded = T < kRecInit ? T : kRecInit;
+    for (int p0 = 0; p0 < loaded; p0 += 32)
+      load_records(recs, P.rec, meta_a, meta_b, nb, p0, loaded - p0 < 32 ? loaded - p0 : 32,
+                   lane);
+    cp_commit();
+
+    // step size and routing of token `lane` (loads overlap the copies)
+    int nseg = -1, nh = 0, ne = 0;
+    float s_tok = 0.f;
+    if (mine) {
+      s_tok = __ldg(P.step + (e - P.epoch0));
+      const int d = cend - cb;
+      nh = hop + 1;
+      ne = e;
+      if (nh == d) {
+        nh = 0;
+        ne = e + 1;
+      }
+      if (ne < epoch_end) {
+        const uint4 key = philox4x32_10(
+            make_uint4(uint32_t(j), uint32_t(ne), 0u, kTagItinerary), seed);
+        nseg = __ldg(P.col_segs + cb + itinerary_slot(uint32_t(nh), uint32_t(d), key));
+      }
+    }
+    if (mine) {
+      meta_a[rank].z = e;
+    }
+    cp_wait_all();
+    __syncwarp();
+
+    // ---- 5a. cold start of the row ring: positions 0 .. R-2
+    int win = -1;  // lane L < R: row of the latest position p with p % R == L
+    int dflag = 0; // lane L < R: that position is loaded directly (hazard)
+    auto prefetch = [&](int pp) {
+      const int slot = pp % R;
+      const int row = recs[pp % kRecBuf].x;
+      const bool hz = __ballot_sync(kFull, lane < R && lane != slot && win == row) != 0u;
+      if (!hz) {
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+          const int idx = lane + 32 * cc;
+          if (idx < k4)
+            cp_async16(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
+        }
+      }
+      if (lane == slot) {
+        win = row;
+        dflag = hz ? 1 : 0;
+      }
+    };
+    // one commit group per position: at tick t exactly R-1 groups are
+    // younger than position t's group, so cp.async.wait_group R-1 suffices
+    for (int pp = 0; pp < R - 1; ++pp) {
+      if (pp < T) prefetch(pp);
+      cp_commit();
+    }
+    int q2 = -1;
+    if (mine && nseg >= 0) q2 = __ldg(P.seg_worker + nseg);
+
+    // ---- 5b. the stream
+    int k = -1, vend = 0, vsoff = 0, vlane = 0, vseg = 0;
+    int64_t vbeg = 0;
+    float s = 0.f;
+    float4 h[CPL];
+#pragma unroll
+    for (int cc = 0; cc < CPL; ++cc) h[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = 0; t < T; ++t) {
+      if (t == vend) {  // a visit starts
+        ++k;
+        const int4 ma = meta_a[k];
+        const int4 mb = meta_b[k];
+        vsoff = t;
+        vend = t + ma.y;
+        vseg = ma.w;
+        vlane = mb.z;
+        vbeg = (int64_t(mb.y) << 32) | uint32_t(mb.x);
+        s = __shfl_sync(kFull, s_tok, vlane);
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc)  // lanes past k/4 hold zeros, never smem
+          h[cc] = lane + 32 * cc < k4 ? hbuf[(k * CPL + cc) * 32 + lane]
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (DEBUG && lane == 0) {
+          const uint32_t tk = atomicAdd(P.log_ticket, 1u);
+          if (int64_t(tk) < P.log_cap) {
+            P.log_seg[tk] = vseg;
+            P.log_epoch[tk] = ma.z;
+          }
+          if (atomicExch(P.owner + ma.x, q) != -1) flag_ownership(P, q, ma.x);
+        }
+      }
+      // keep the records one chunk ahead of the row prefetch
+      if (loaded < T && loaded < t + R + 32) {
+        const int cnt = T - loaded < 32 ? T - loaded : 32;
+        load_records(recs, P.rec, meta_a, meta_b, nb, loaded, cnt, lane);
+        loaded += cnt;
+      }
+      const int pp = t + R - 1;
+      if (pp < T) {
+        prefetch(pp);
+      } else if (lane == pp % R) {
+        win = -1;
+        dflag = 0;
+      }
+      cp_commit();
+      cp_wait<R - 1>();
+      __syncwarp();
+
+      const int2 rc = recs[t % kRecBuf];
+      const int slot = t % R;
+      const int direct = __shfl_sync(kFull, dflag, slot);
+      float4* wrow = W4 + int64_t(rc.x) * pitch4;
+      float4 w[CPL];
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int idx = lane + 32 * cc;
+        w[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < k4) w[cc] = direct ? __ldcg(wrow + idx) : rows[(slot * CPL + cc) * 32 + lane];
+      }
+      float part = 0.f;
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        part = fmaf(w[cc].x, h[cc].x, part);
+        part = fmaf(w[cc].y, h[cc].y, part);
+        part = fmaf(w[cc].z, h[cc].z, part);
+        part = fmaf(w[cc].w, h[cc].w, part);
+      }
+      const float err = __int_as_float(rc.y) - warp_sum(part);
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int idx = lane + 32 * cc;
+        float4 wn, hn;
+        wn.x = fmaf(s, fmaf(err, h[cc].x, -lam * w[cc].x), w[cc].x);
+        wn.y = fmaf(s, fmaf(err, h[cc].y, -lam * w[cc].y), w[cc].y);
+        wn.z = fmaf(s, fmaf(err, h[cc].z, -lam * w[cc].z), w[cc].z);
+        wn.w = fmaf(s, fmaf(err, h[cc].w, -lam * w[cc].w), w[cc].w);
+        hn.x = fmaf(s, fmaf(err, w[cc].x, -lam * h[cc].x), h[cc].x);
+        hn.y = fmaf(s, fmaf(err, w[cc].y, -lam * h[cc].y), h[cc].y);
+        hn.z = fmaf(s, fmaf(err, w[cc].z, -lam * h[cc].z), h[cc].z);
+        hn.w = fmaf(s, fmaf(err, w[cc].w, -lam * h[cc].w), h[cc].w);
+        if (idx < k4) {
+          wrow[idx] = wn;
+          h[cc] = hn;
+        }
+      }
+      if (DEBUG && lane == 0) P.rec_count[vbeg + (t - vsoff)] += 1;
+
+      if (t == vend - 1) {  // the visit ends: publish h_j
+        const int jv = meta_a[k].x;
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+          const int idx = lane + 32 * cc;
+          if (idx < k4) __stcg(H4 + int64_t(jv) * pitch4 + idx, h[cc]);
+        }
+        if (vend - vsoff >= kHeavy) {  // long visit: hand the token on now
+          if (lane == vlane) {
+            __stcg(P.tok_hop + j, nh);
+            __stcg(P.tok_epoch + j, ne);
+            if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
+          }
+          __syncwarp();
+          if (lane == vlane && nseg >= 0) {
+            __threadfence();
+            push_token(P, q2, uint32_t(nseg));
+          }
+        }
+      }
+    }
+
+    // ---- 6. hand on the remaining tokens together
+    const bool late = mine && c < kHeavy;
+    if (late) {
+      __stcg(P.tok_hop + j, nh);
+      __stcg(P.tok_epoch + j, ne);
+      if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
+    }
+    __syncwarp();
+    if (__any_sync(kFull, late && nseg >= 0)) {
+      __threadfence();
+      if (late && nseg >= 0) push_token(P, q2, uint32_t(nseg));
+    }
+  }
+}
+
+template <int CPL>
+const void* batched_ptr(bool debug) {
+  return debug ? (const void*)nomad_batched_kernel<CPL, true>
+               : (const void*)nomad_batched_kernel<CPL, false>;
+}
+
+}  // namespace
+
+// Kernel pointer and per-warp shared memory (bytes) of the batched kernel.
+const void* batched_kernel(int k4, bool debug, size_t* smem_per_warp) {
+  if (k4 <= 32) {
+    *smem_per_warp = sizeof(float4) * warp_smem_f4<1>();
+    return batched_ptr<1>(debug);
+  }
+  if (k4 <= 64) {
+    *smem_per_warp = sizeof(float4) * warp_smem_f4<2>();
+    return batched_ptr<2>(debug);
+  }
+  if (k4 <= 128) {
+    *smem_per_warp = sizeof(float4) * warp_smem_f4<4>();
+    return batched_ptr<4>(debug);
+  }
+  return nullptr;
+}
+
+}  // namespace nomad

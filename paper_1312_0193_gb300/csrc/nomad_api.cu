@@ -134,9 +134,6 @@ void dev_free(nomad_handle* h, void** p) {
   *p = nullptr;
 }
 
-int max_resident_workers(int device, int warps_per_block, int k4, int precision,
-                         int* blocks_per_sm);
-int default_warps_per_block();
 
 }  // namespace nomad
 
@@ -159,6 +156,7 @@ void nomad_schedule_default(nomad_schedule* s) {
   s->spin_timeout_ns = 0;
   s->device = 0;
   s->debug_drop_item = -1;
+  s->variant = NOMAD_VARIANT_BATCHED;
 }
 
 const char* nomad_error_string(int32_t code) {
@@ -192,7 +190,8 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
       !std::isfinite(sched.beta) || sched.alpha < 0.f || sched.beta < 0.f ||
       (sched.mode != NOMAD_MODE_EPOCH && sched.mode != NOMAD_MODE_UNIFORM) ||
       (sched.partition != NOMAD_PARTITION_RATINGS && sched.partition != NOMAD_PARTITION_USERS) ||
-      sched.n_workers < 0 || sched.warps_per_block < 0 || sched.spin_timeout_ns < 0)
+      sched.n_workers < 0 || sched.warps_per_block < 0 || sched.spin_timeout_ns < 0 ||
+      (sched.variant != NOMAD_VARIANT_BATCHED && sched.variant != NOMAD_VARIANT_SIMPLE))
     return NOMAD_ERR_INVALID_ARG;
   if (sched.precision != NOMAD_FP32) return NOMAD_ERR_UNSUPPORTED;
   int ndev = 0;
@@ -215,7 +214,7 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
                                                  : default_warps_per_block();
   int bps = 0;
   const int pmax = max_resident_workers(h->device, h->warps_per_block, h->k4, sched.precision,
-                                        &bps);
+                                        sched.mode, sched.variant, &bps);
   if (pmax <= 0) {
     delete h;
     return NOMAD_ERR_UNSUPPORTED;

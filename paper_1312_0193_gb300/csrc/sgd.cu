@@ -25,92 +25,12 @@
 // tokens than its capacity (epoch mode: the number of items the worker
 // holds; uniform mode: n), so a position is reused only after its previous
 // payload was consumed.
-#include "nomad_internal.cuh"
+#include "sgd_common.cuh"
 
 namespace nomad {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kPrefetch = 4;   // W rows in flight per worker
-constexpr int kDefaultWarpsPerBlock = 8;
-constexpr int kMaxWarpsPerBlock = 16;
-
-__device__ __forceinline__ float warp_sum(float v) {
-  v += __shfl_xor_sync(kFull, v, 16);
-  v += __shfl_xor_sync(kFull, v, 8);
-  v += __shfl_xor_sync(kFull, v, 4);
-  v += __shfl_xor_sync(kFull, v, 2);
-  v += __shfl_xor_sync(kFull, v, 1);
-  return v;
-}
-
-// Position `hop` of item j's visit order in one epoch: a bijection of
-// [0, d) built from two rounds of (odd multiply + add) mod 2^b and xorshift,
-// walked until it lands in [0, d).  The walk ends within 2^b < 2d steps.
-__device__ __forceinline__ uint32_t itinerary_slot(uint32_t hop, uint32_t d,
-                                                   uint4 key) {
-  if (d <= 1) return 0;
-  const int b = 32 - __clz(d - 1);
-  const uint32_t mask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
-  const int sh = (b + 1) >> 1;
-  uint32_t x = hop;
-  for (uint32_t guard = 0; guard <= mask; ++guard) {
-    x = (x * (key.x | 1u) + key.y) & mask;
-    x ^= x >> sh;
-    x = (x * (key.z | 1u) + key.w) & mask;
-    x ^= x >> sh;
-    if (x < d) return x;
-  }
-  return hop;  // not reached: the orbit of hop returns to [0, d)
-}
-
-__device__ __forceinline__ void push_token(const SgdParams& P, int q,
-                                           uint32_t payload) {
-  const uint32_t pos = atomicAdd(P.ring_tail + q, 1u);
-  const int lg = P.ring_log2[q];
-  unsigned long long* slot = P.ring + P.ring_base[q] + (pos & ((1u << lg) - 1u));
-  st_release_u64(slot, (static_cast<unsigned long long>(pos >> lg) << 32) | payload);
-}
-
-// Lane 0 only.  Returns the payload at position `head` of worker q's ring,
-// or -1 when the wait gave up (another worker failed, the stop flag of
-// uniform mode was raised, or this wait exceeded the timeout, in which case
-// the status word records it).
-__device__ int pop_token(const SgdParams& P, int q, uint32_t head, int lg,
-                         const unsigned long long* ring_q) {
-  const unsigned long long* slot = ring_q + (head & ((1u << lg) - 1u));
-  const uint32_t lap = head >> lg;
-  unsigned long long v = ld_acquire_u64(slot);
-  if (uint32_t(v >> 32) == lap) return int(uint32_t(v));
-  const unsigned long long t0 = globaltimer_ns();
-  const unsigned long long max_iters =
-      static_cast<unsigned long long>(P.timeout_ns) / 16ull + (1ull << 20);
-  unsigned ns = 32;
-  for (unsigned long long it = 0; it < max_iters; ++it) {
-    v = ld_acquire_u64(slot);
-    if (uint32_t(v >> 32) == lap) return int(uint32_t(v));
-    if ((it & 15) == 15) {
-      if (ld_relaxed_i32(P.status) != 0) return -1;
-      if (P.stop != nullptr && ld_relaxed_i32(P.stop) != 0) return -1;
-      if (globaltimer_ns() - t0 > static_cast<unsigned long long>(P.timeout_ns)) break;
-    }
-    __nanosleep(ns);
-    if (ns < 512) ns <<= 1;
-  }
-  if (atomicCAS(P.status, 0, NOMAD_ERR_TIMEOUT) == 0) {
-    atomicExch(P.status + 1, q);
-    atomicExch(P.status + 2, int(head));
-  }
-  return -1;
-}
-
-__device__ __forceinline__ void flag_ownership(const SgdParams& P, int q, int j) {
-  atomicAdd(P.status + 3, 1);
-  if (atomicCAS(P.status, 0, NOMAD_ERR_OWNERSHIP) == 0) {
-    atomicExch(P.status + 1, q);
-    atomicExch(P.status + 2, j);
-  }
-}
+constexpr int kPrefetch = 4;   // W rows in flight per worker (simple kernel)
 
 template <int CPL>
 __device__ __forceinline__ void load_row(float4 (&w)[CPL], const float4* row,
@@ -417,35 +337,42 @@ const void* epoch_kernel_ptr(bool debug, int mode) {
                : (const void*)nomad_epoch_kernel<CPL, false>;
 }
 
-const void* kernel_for(int k4, bool debug, int mode) {
+}  // namespace
+
+// The worker kernel for a handle's settings and its dynamic shared memory per
+// warp (bytes).
+const void* worker_kernel(int k4, bool debug, int mode, int variant, size_t* smem_per_warp) {
+  *smem_per_warp = 0;
+  if (mode == NOMAD_MODE_EPOCH && variant == NOMAD_VARIANT_BATCHED)
+    return batched_kernel(k4, debug, smem_per_warp);
   if (k4 <= 32) return epoch_kernel_ptr<1>(debug, mode);
   if (k4 <= 64) return epoch_kernel_ptr<2>(debug, mode);
   if (k4 <= 128) return epoch_kernel_ptr<4>(debug, mode);
   return nullptr;
 }
 
-}  // namespace
-
-int max_resident_workers(int device, int warps_per_block, int k4, int precision,
-                         int* blocks_per_sm) {
+int max_resident_workers(int device, int warps_per_block, int k4, int precision, int mode,
+                         int variant, int* blocks_per_sm) {
   (void)precision;
   if (warps_per_block <= 0) warps_per_block = kDefaultWarpsPerBlock;
   if (warps_per_block > kMaxWarpsPerBlock) return -1;
-  const void* fn = kernel_for(k4, false, NOMAD_MODE_EPOCH);
-  if (!fn) return -1;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps_per_block * 32, 0) !=
-      cudaSuccess)
-    return -1;
-  // the debug and uniform variants must fit the same grid
-  for (int mode = 0; mode < 2; ++mode)
-    for (int dbg = 0; dbg < 2; ++dbg) {
-      int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel_for(k4, dbg, mode),
-                                                        warps_per_block * 32, 0) != cudaSuccess)
-        return -1;
-      if (b < per_sm) per_sm = b;
-    }
+  int per_sm = 1 << 30;
+  // the debug variant must fit the same grid
+  for (int dbg = 0; dbg < 2; ++dbg) {
+    size_t spw = 0;
+    const void* fn = worker_kernel(k4, dbg, mode, variant, &spw);
+    if (!fn) return -1;
+    const size_t smem = spw * warps_per_block;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+            cudaSuccess)
+      return -1;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, warps_per_block * 32, smem) !=
+        cudaSuccess)
+      return -1;
+    if (b < per_sm) per_sm = b;
+  }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (blocks_per_sm) *blocks_per_sm = per_sm;
@@ -520,7 +447,9 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   ++h->launches;
   if (h->nnz == 0) return NOMAD_OK;
 
-  const void* fn = kernel_for(h->k4, debug, h->sched.mode);
+  size_t spw = 0;
+  const void* fn = worker_kernel(h->k4, debug, h->sched.mode, h->sched.variant, &spw);
+  const size_t smem = spw * size_t(h->warps_per_block);
   void* args[] = {&P};
   if (!h->ev_start) {
     if (cudaEventCreate(&h->ev_start) != cudaSuccess ||
@@ -530,8 +459,8 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
     }
   }
   cudaEventRecord(h->ev_start, st);
-  e = cudaLaunchCooperativeKernel(fn, dim3(h->blocks), dim3(h->warps_per_block * 32), args, 0,
-                                  st);
+  e = cudaLaunchCooperativeKernel(fn, dim3(h->blocks), dim3(h->warps_per_block * 32), args,
+                                  smem, st);
   if (e != cudaSuccess) {
     h->last_error = std::string("epoch: cooperative launch: ") + cudaGetErrorString(e);
     return NOMAD_ERR_CUDA;

@@ -1,0 +1,93 @@
+// sgd_common.cuh -- device helpers shared by the NOMAD worker kernels:
+// the epoch-mode visit order, the ring-queue push and the bounded pop.
+#pragma once
+
+#include "nomad_internal.cuh"
+
+namespace nomad {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kDefaultWarpsPerBlock = 8;
+constexpr int kMaxWarpsPerBlock = 16;
+
+__device__ __forceinline__ float warp_sum(float v) {
+  v += __shfl_xor_sync(kFull, v, 16);
+  v += __shfl_xor_sync(kFull, v, 8);
+  v += __shfl_xor_sync(kFull, v, 4);
+  v += __shfl_xor_sync(kFull, v, 2);
+  v += __shfl_xor_sync(kFull, v, 1);
+  return v;
+}
+
+// Position `hop` of item j's visit order in one epoch: a bijection of
+// [0, d) built from two rounds of (odd multiply + add) mod 2^b and xorshift,
+// walked until it lands in [0, d).  The walk ends within 2^b < 2d steps.
+__device__ __forceinline__ uint32_t itinerary_slot(uint32_t hop, uint32_t d,
+                                                   uint4 key) {
+  if (d <= 1) return 0;
+  const int b = 32 - __clz(d - 1);
+  const uint32_t mask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
+  const int sh = (b + 1) >> 1;
+  uint32_t x = hop;
+  for (uint32_t guard = 0; guard <= mask; ++guard) {
+    x = (x * (key.x | 1u) + key.y) & mask;
+    x ^= x >> sh;
+    x = (x * (key.z | 1u) + key.w) & mask;
+    x ^= x >> sh;
+    if (x < d) return x;
+  }
+  return hop;  // not reached: the orbit of hop returns to [0, d)
+}
+
+__device__ __forceinline__ void push_token(const SgdParams& P, int q,
+                                           uint32_t payload) {
+  const uint32_t pos = atomicAdd(P.ring_tail + q, 1u);
+  const int lg = P.ring_log2[q];
+  unsigned long long* slot = P.ring + P.ring_base[q] + (pos & ((1u << lg) - 1u));
+  st_release_u64(slot, (static_cast<unsigned long long>(pos >> lg) << 32) | payload);
+}
+
+// Lane 0 only.  Returns the payload at position `head` of worker q's ring,
+// or -1 when the wait gave up (another worker failed, the stop flag of
+// uniform mode was raised, or this wait exceeded the timeout, in which case
+// the status word records it).
+__device__ int pop_token(const SgdParams& P, int q, uint32_t head, int lg,
+                         const unsigned long long* ring_q) {
+  const unsigned long long* slot = ring_q + (head & ((1u << lg) - 1u));
+  const uint32_t lap = head >> lg;
+  unsigned long long v = ld_acquire_u64(slot);
+  if (uint32_t(v >> 32) == lap) return int(uint32_t(v));
+  const unsigned long long t0 = globaltimer_ns();
+  const unsigned long long max_iters =
+      static_cast<unsigned long long>(P.timeout_ns) / 16ull + (1ull << 20);
+  unsigned ns = 32;
+  for (unsigned long long it = 0; it < max_iters; ++it) {
+    v = ld_acquire_u64(slot);
+    if (uint32_t(v >> 32) == lap) return int(uint32_t(v));
+    if ((it & 15) == 15) {
+      if (ld_relaxed_i32(P.status) != 0) return -1;
+      if (P.stop != nullptr && ld_relaxed_i32(P.stop) != 0) return -1;
+      if (globaltimer_ns() - t0 > static_cast<unsigned long long>(P.timeout_ns)) break;
+    }
+    __nanosleep(ns);
+    if (ns < 128) ns <<= 1;
+  }
+  if (atomicCAS(P.status, 0, NOMAD_ERR_TIMEOUT) == 0) {
+    atomicExch(P.status + 1, q);
+    atomicExch(P.status + 2, int(head));
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void flag_ownership(const SgdParams& P, int q, int j) {
+  atomicAdd(P.status + 3, 1);
+  if (atomicCAS(P.status, 0, NOMAD_ERR_OWNERSHIP) == 0) {
+    atomicExch(P.status + 1, q);
+    atomicExch(P.status + 2, j);
+  }
+}
+
+
+}  // namespace
+}  // namespace nomad

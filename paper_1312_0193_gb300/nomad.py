@@ -33,6 +33,8 @@ NOMAD_FP32 = 0
 NOMAD_BF16 = 1
 NOMAD_PARTITION_RATINGS = 0
 NOMAD_PARTITION_USERS = 1
+NOMAD_VARIANT_BATCHED = 0
+NOMAD_VARIANT_SIMPLE = 1
 NOMAD_COO = 0
 NOMAD_CSC = 1
 
@@ -44,7 +46,8 @@ class nomad_schedule(ctypes.Structure):
                 ("warps_per_block", ctypes.c_int32), ("debug", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("spin_timeout_ns", ctypes.c_int64),
                 ("device", ctypes.c_int32), ("debug_drop_item", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 6)]
+                ("variant", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 5)]
 
 
 class nomad_info(ctypes.Structure):
@@ -213,7 +216,7 @@ class Nomad:
     def __init__(self, m, n, k, lam, alpha=0.012, beta=0.05, mode="epoch",
                  precision="fp32", partition="ratings", n_workers=0,
                  warps_per_block=0, debug=False, seed=1, spin_timeout_ns=0,
-                 device=0, debug_drop_item=-1):
+                 device=0, debug_drop_item=-1, variant="batched"):
         s = nomad_schedule_default()
         s.alpha, s.beta = alpha, beta
         s.mode = {"epoch": NOMAD_MODE_EPOCH, "uniform": NOMAD_MODE_UNIFORM}[mode]
@@ -227,6 +230,7 @@ class Nomad:
         s.spin_timeout_ns = spin_timeout_ns
         s.device = device
         s.debug_drop_item = debug_drop_item
+        s.variant = {"batched": NOMAD_VARIANT_BATCHED, "simple": NOMAD_VARIANT_SIMPLE}[variant]
         self.schedule = s
         self.m, self.n, self.k, self.lam = m, n, k, lam
         self.h = nomad_create(m, n, k, lam, s)

@@ -167,16 +167,27 @@ def replay_check(r, k, lam, alpha, beta, epochs, p=None, calls=1, **kw):
     return Wg, Hg
 
 
-def test_replay_tiny_paper_schedule(tiny):
+@pytest.mark.parametrize("variant", ["batched", "simple"])
+def test_replay_tiny_paper_schedule(tiny, variant):
     """Tiny planted config, the paper's decaying step size (alpha 0.012, beta
     0.05), 20 epochs, replayed on the oracle."""
-    replay_check(tiny, 10, 0.05, 0.012, 0.05, 20, p=64)
+    replay_check(tiny, 10, 0.05, 0.012, 0.05, 20, p=64, variant=variant)
 
 
-def test_replay_tiny_large_steps(tiny):
+@pytest.mark.parametrize("variant", ["batched", "simple"])
+def test_replay_tiny_large_steps(tiny, variant):
     """Larger steps (alpha 0.1, beta 0.01) move the factors far from the
     start, so the comparison is sensitive to any arithmetic difference."""
-    replay_check(tiny, 10, 0.05, 0.1, 0.01, 20, p=64)
+    replay_check(tiny, 10, 0.05, 0.1, 0.01, 20, p=64, variant=variant)
+
+
+@pytest.mark.parametrize("p", [4, 16])
+def test_replay_few_workers_long_visits(p):
+    """Few workers: long visits (>= 32 ratings, pushed right after their
+    visit), many rows shared between the visits of one batch (the
+    prefetch-hazard path), records streamed in several chunks."""
+    r = synth.netflix_shaped(0.002, seed=13)
+    replay_check(r, 100, 0.05, 0.01, 0.05, 2, p=p)
 
 
 def test_replay_auto_workers_two_calls(tiny):
