@@ -219,6 +219,36 @@ NOMAD_API int nomad_get_replay_log(nomad_t *h, int64_t cap, int32_t *seg, int32_
 NOMAD_API int nomad_get_debug_counts(nomad_t *h, int32_t *rec_count,
                            int64_t *ownership_violations);
 
+/* Largest number of 8192-rating tiles nomad_rmse_noalloc can reduce: its
+ * partial sums live in a fixed __device__ array of this many doubles
+ * (512 KiB, held by every GPU that loads the library until exit). */
+#define NOMAD_NOALLOC_MAX_TILES 65536
+
+/* Test RMSE for callers that cannot let the library allocate memory (the
+ * paper has no counterpart: this serves deployment, not the method).  For
+ * example a service that reserves all device memory up front, or a loop that
+ * must not take the implicit device synchronisation of cudaMalloc/cudaFree.
+ * It needs no handle and calls no allocator: everything is caller memory
+ * except a fixed scratch array inside the library.
+ *  W (m x pitch), H (n x pitch): binary32 factors in device memory, row
+ *    major, entries 0..k-1 of each row used; 1 <= k <= 512, pitch >= k.
+ *  rows, cols, vals: nnz test ratings in device memory.
+ *  out: one double in device memory; receives sqrt(sum (A_ij -
+ *    <w_i,h_j>)^2 / nnz) (binary32 residuals, binary64 sums), or NaN when
+ *    nnz is 0 or an index lies outside [0,m) x [0,n).
+ * Asynchronous on `stream` (a cudaStream_t as void*), on the current device.
+ * Rejects nnz > NOMAD_NOALLOC_MAX_TILES * 8192 (536,870,912) with
+ * NOMAD_ERR_INVALID_ARG.  The first call on a device looks up the scratch
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the scratch array: calls
+ * whose work may overlap on the GPU (unordered streams) race and must not
+ * be issued. */
+NOMAD_API int nomad_rmse_noalloc(const float *W, const float *H, int64_t m,
+                                 int64_t n, int32_t k, int64_t pitch,
+                                 int64_t nnz, const int32_t *rows,
+                                 const int32_t *cols, const float *vals,
+                                 double *out, void *stream);
+
 /* Free every resource of the handle (NULL is ignored). */
 NOMAD_API void nomad_destroy(nomad_t *h);
 

@@ -81,6 +81,8 @@ SIGNATURES = {
     "nomad_get_layout": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "nomad_get_replay_log": (_I32, [_P, _I64, _P, _P, ctypes.POINTER(_I64)]),
     "nomad_get_debug_counts": (_I32, [_P, _P, ctypes.POINTER(_I64)]),
+    "nomad_rmse_noalloc": (_I32, [_P, _P, _I64, _I64, _I32, _I64, _I64, _P, _P, _P, _P,
+                                  _P]),
     "nomad_destroy": (None, [_P]),
     "nomad_error_string": (ctypes.c_char_p, [_I32]),
     "nomad_last_error_message": (ctypes.c_char_p, [_P]),
