@@ -59,6 +59,15 @@ def _lib():
         lib.orc_shuffled_sgd.argtypes = [i32, f64, f64, f64, i64, P, P, P, i32,
                                          u64, P, P, P]
         lib.orc_shuffled_sgd.restype = i32
+        lib.orc_bf16_rn_n.argtypes = [i64, P, P]
+        lib.orc_bf16_rn_n.restype = None
+        lib.orc_bf16_sr_n.argtypes = [i64, P, P, P]
+        lib.orc_bf16_sr_n.restype = None
+        lib.orc_bf16_to_f32_n.argtypes = [i64, P, P]
+        lib.orc_bf16_to_f32_n.restype = None
+        lib.orc_replay_bf16.argtypes = [i32, f32, f64, f64, i64, P, P, i64, P, P,
+                                        P, P, P, P, P, u64]
+        lib.orc_replay_bf16.restype = i32
         _LIB = lib
     return _LIB
 
@@ -287,3 +296,56 @@ def shuffled_sgd(rows, cols, vals, W, H, lam: float, alpha: float, beta: float,
     if rc != 0:
         raise MemoryError("shuffled_sgd")
     return W, H, cnt
+
+
+# ---------------------------------------------------------------- bfloat16
+def bf16_rn(x) -> np.ndarray:
+    """bfloat16 bit patterns (uint16) of binary32 values, round to nearest
+    even."""
+    x = _c(x, np.float32)
+    out = np.zeros(x.shape, dtype=np.uint16)
+    _lib().orc_bf16_rn_n(x.size, _ptr(x), _ptr(out))
+    return out
+
+
+def bf16_sr(x, r16) -> np.ndarray:
+    """Stochastic rounding of binary32 values to bfloat16 with the given 16
+    random bits per value."""
+    x = _c(x, np.float32)
+    r = _c(r16, np.uint32)
+    assert r.shape == x.shape
+    out = np.zeros(x.shape, dtype=np.uint16)
+    _lib().orc_bf16_sr_n(x.size, _ptr(x), _ptr(r), _ptr(out))
+    return out
+
+
+def bf16_to_f32(b) -> np.ndarray:
+    b = _c(b, np.uint16)
+    out = np.zeros(b.shape, dtype=np.float32)
+    _lib().orc_bf16_to_f32_n(b.size, _ptr(b), _ptr(out))
+    return out
+
+
+def replay_bf16(layout: dict, visit_seg, visit_epoch, Wb, Hb, lam: float,
+                alpha: float, beta: float, seed: int, rec_count=None):
+    """Replay with bfloat16 storage and stochastic rounding (see the C
+    source).  Wb, Hb are uint16 bit patterns (m x k, n x k).  Returns
+    (Wb, Hb, rec_count)."""
+    visit_seg = _c(visit_seg, np.int64)
+    visit_epoch = _c(visit_epoch, np.int32)
+    assert visit_seg.shape == visit_epoch.shape
+    Wb = _c(Wb, np.uint16).copy()
+    Hb = _c(Hb, np.uint16).copy()
+    seg_col = _c(layout["seg_col"], np.int32)
+    rec_row = _c(layout["rec_row"], np.int32)
+    rec_val = _c(layout["rec_val"], np.float32)
+    cnt = (np.zeros(rec_row.size, dtype=np.int32) if rec_count is None
+           else _c(rec_count, np.int32).copy())
+    rc = _lib().orc_replay_bf16(Wb.shape[1], lam, alpha, beta, visit_seg.size,
+                                _ptr(visit_seg), _ptr(visit_epoch), seg_col.size,
+                                _ptr(layout["seg_ptr"]), _ptr(seg_col),
+                                _ptr(rec_row), _ptr(rec_val), _ptr(Wb), _ptr(Hb),
+                                _ptr(cnt), seed)
+    if rc != 0:
+        raise ValueError("replay_bf16: bad segment index or allocation failure")
+    return Wb, Hb, cnt

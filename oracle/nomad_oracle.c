@@ -409,3 +409,103 @@ int32_t orc_shuffled_sgd(int32_t k, double lambda, double alpha, double beta,
   free(perm);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* bfloat16 storage (the precision variant of the GPU path: W and H stored  */
+/* as bfloat16, every update computed in binary32, stochastic rounding on   */
+/* write-back).  A bfloat16 is the upper 16 bits of a binary32.             */
+/*                                                                          */
+/* Round to nearest, ties to even (used for the initial values):            */
+/*   add 0x7fff plus the lowest kept bit, then truncate.                    */
+/* Stochastic rounding with 16 random bits r: add r to the 16 dropped bits  */
+/* of the magnitude and truncate, so the magnitude rounds up with           */
+/* probability (dropped bits) / 2^16 and the expected value is exact.       */
+/* Infinities and NaN are truncated (NaN kept quiet).                       */
+/* ------------------------------------------------------------------------ */
+static uint32_t f32_bits(float x) { uint32_t u; memcpy(&u, &x, 4); return u; }
+static float bits_f32(uint32_t u) { float x; memcpy(&x, &u, 4); return x; }
+
+uint16_t orc_bf16_rn(float x) {
+  uint32_t u = f32_bits(x);
+  if ((u & 0x7f800000u) == 0x7f800000u)
+    return (uint16_t)((u >> 16) | ((u & 0x007fffffu) ? 0x0040u : 0u));
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+uint16_t orc_bf16_sr(float x, uint32_t r16) {
+  uint32_t u = f32_bits(x);
+  if ((u & 0x7f800000u) == 0x7f800000u)
+    return (uint16_t)((u >> 16) | ((u & 0x007fffffu) ? 0x0040u : 0u));
+  u += (r16 & 0xffffu);
+  return (uint16_t)(u >> 16);
+}
+
+float orc_bf16_to_f32(uint16_t b) { return bits_f32((uint32_t)b << 16); }
+
+/* The 16 random bits for entry l of a row written back by the update of
+ * record r in epoch e (factor W) or by the end of the visit of segment s in
+ * epoch e (factor H): Philox4x32-10 with key = seed and counter
+ * (r_lo, r_hi, e, 0x57000000 | l/4) for W, (s, e, 0, 0x48000000 | l/4) for
+ * H; entry l takes word (l mod 4)/2 (W) or 2 + (l mod 4)/2 (H), its low half
+ * for even l and high half for odd l. */
+static uint32_t sr_bits(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                        uint32_t tag, int32_t l, int word_base) {
+  uint32_t w = rand_word(seed, c0, c1, c2, tag | (uint32_t)(l / 4),
+                         word_base + (l % 4) / 2);
+  return (l % 2) ? (w >> 16) : (w & 0xffffu);
+}
+
+/* Replay in bfloat16 storage: W and H are arrays of bfloat16 bit patterns,
+ * rows of k entries.  Per visit: h_j is widened to binary32, every rating of
+ * the segment is applied in binary32 (same update as orc_sgd_update_f32) and
+ * w_i is written back with stochastic rounding; at the end of the visit h_j
+ * is written back with stochastic rounding.  visit_epoch[v] is the epoch of
+ * visit v (it enters the rounding counters); the step size comes from the
+ * per-record update count as in the other replays. */
+int32_t orc_replay_bf16(int32_t k, float lambda, double alpha, double beta,
+                        int64_t n_visits, const int64_t *visit_seg,
+                        const int32_t *visit_epoch, int64_t n_seg,
+                        const int64_t *seg_ptr, const int32_t *seg_col,
+                        const int32_t *rec_row, const float *rec_val,
+                        uint16_t *W, uint16_t *H, int32_t *rec_count,
+                        uint64_t seed) {
+  float *h = (float *)malloc(sizeof(float) * (size_t)k);
+  float *w = (float *)malloc(sizeof(float) * (size_t)k);
+  if (!h || !w) { free(h); free(w); return -2; }
+  for (int64_t v = 0; v < n_visits; ++v) {
+    const int64_t s = visit_seg[v];
+    if (s < 0 || s >= n_seg) { free(h); free(w); return -1; }
+    const uint32_t e = (uint32_t)visit_epoch[v];
+    uint16_t *hb = H + (int64_t)seg_col[s] * k;
+    for (int32_t l = 0; l < k; ++l) h[l] = orc_bf16_to_f32(hb[l]);
+    for (int64_t r = seg_ptr[s]; r < seg_ptr[s + 1]; ++r) {
+      uint16_t *wb = W + (int64_t)rec_row[r] * k;
+      for (int32_t l = 0; l < k; ++l) w[l] = orc_bf16_to_f32(wb[l]);
+      const float step = (float)orc_step_size(alpha, beta, rec_count[r]);
+      orc_sgd_update_f32(k, w, h, rec_val[r], lambda, step);
+      for (int32_t l = 0; l < k; ++l)
+        wb[l] = orc_bf16_sr(w[l], sr_bits(seed, (uint32_t)r,
+                                          (uint32_t)((uint64_t)r >> 32), e,
+                                          0x57000000u, l, 0));
+      rec_count[r] += 1;
+    }
+    for (int32_t l = 0; l < k; ++l)
+      hb[l] = orc_bf16_sr(h[l], sr_bits(seed, (uint32_t)s, e, 0u, 0x48000000u,
+                                        l, 2));
+  }
+  free(h);
+  free(w);
+  return 0;
+}
+
+/* Array forms of the conversions above (for the Python side). */
+void orc_bf16_rn_n(int64_t n, const float *x, uint16_t *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_bf16_rn(x[i]);
+}
+void orc_bf16_sr_n(int64_t n, const float *x, const uint32_t *r16, uint16_t *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_bf16_sr(x[i], r16[i]);
+}
+void orc_bf16_to_f32_n(int64_t n, const uint16_t *b, float *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_bf16_to_f32(b[i]);
+}
