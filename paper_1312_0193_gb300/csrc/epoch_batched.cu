@@ -41,11 +41,47 @@ struct RowRing {
   static constexpr int R = 16 / CPL;  // slots; R-1 rows in flight
 };
 
-// Shared memory of one warp, in float4 units: row slots, h of the batch,
-// records (int2, two per float4), and two int4 tables of batch metadata.
-template <int CPL>
-__host__ __device__ constexpr int warp_smem_f4() {
-  return RowRing<CPL>::R * CPL * 32 + kBatch * CPL * 32 + kRecBuf / 2 + 2 * kBatch;
+// Storage of W and H: binary32 (a chunk of 4 entries is a float4) or
+// bfloat16 (a chunk is 4 x 16 bits in a uint2).  Arithmetic is binary32 in
+// both cases; bfloat16 rows are widened on load and stochastically rounded on
+// write-back (16 random bits per entry from Philox4x32-10 at counter
+// (record lo, record hi, epoch, 0x57000000 | chunk) for W and
+// (segment, epoch, 0, 0x48000000 | chunk) for H; entry 4c+i takes half i%2 of
+// word i/2, or of word 2 + i/2 for H).
+template <bool BF>
+struct Storage;
+template <>
+struct Storage<false> {
+  using chunk_t = float4;
+  static __device__ __forceinline__ float4 widen(float4 c) { return c; }
+};
+template <>
+struct Storage<true> {
+  using chunk_t = uint2;
+  static __device__ __forceinline__ float4 widen(uint2 c) {
+    return make_float4(__uint_as_float(c.x << 16), __uint_as_float(c.x & 0xffff0000u),
+                       __uint_as_float(c.y << 16), __uint_as_float(c.y & 0xffff0000u));
+  }
+};
+
+// binary32 -> bfloat16 with 16 random bits added to the dropped bits of the
+// magnitude (stochastic rounding); infinities and NaN are truncated.
+__device__ __forceinline__ uint32_t bf16_sr(float x, uint32_t r16) {
+  const uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (u >> 16) | ((u & 0x007fffffu) ? 0x40u : 0u);
+  return (u + (r16 & 0xffffu)) >> 16;
+}
+__device__ __forceinline__ uint2 pack_sr(float4 v, uint32_t ra, uint32_t rb) {
+  return make_uint2(bf16_sr(v.x, ra) | (bf16_sr(v.y, ra >> 16) << 16),
+                    bf16_sr(v.z, rb) | (bf16_sr(v.w, rb >> 16) << 16));
+}
+
+// Shared memory of one warp in bytes: row slots, h of the batch, records
+// (int2) and two int4 tables of batch metadata.
+template <int CPL, bool BF>
+__host__ __device__ constexpr int warp_smem_bytes() {
+  return int((RowRing<CPL>::R + kBatch) * CPL * 32 * sizeof(typename Storage<BF>::chunk_t)) +
+         kRecBuf * 8 + 2 * kBatch * 16;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -81,17 +117,19 @@ __device__ __forceinline__ void load_records(int2* recs, const int2* __restrict_
   }
 }
 
-template <int CPL, bool DEBUG>
+template <int CPL, bool BF, bool DEBUG>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
 nomad_batched_kernel(const SgdParams P) {
   constexpr int R = RowRing<CPL>::R;
+  using chunk_t = typename Storage<BF>::chunk_t;
   extern __shared__ float4 smem_f4[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int q = blockIdx.x * (blockDim.x >> 5) + wib;
   if (q >= P.p) return;
-  float4* rows = smem_f4 + size_t(wib) * warp_smem_f4<CPL>();
-  float4* hbuf = rows + R * CPL * 32;
+  chunk_t* rows = reinterpret_cast<chunk_t*>(reinterpret_cast<unsigned char*>(smem_f4) +
+                                             size_t(wib) * warp_smem_bytes<CPL, BF>());
+  chunk_t* hbuf = rows + R * CPL * 32;
   int2* recs = reinterpret_cast<int2*>(hbuf + kBatch * CPL * 32);
   int4* meta_a = reinterpret_cast<int4*>(recs + kRecBuf);  // {j, c, e, seg}
   int4* meta_b = meta_a + kBatch;                          // {beg_lo, beg_hi, lane, soff}
@@ -100,8 +138,8 @@ nomad_batched_kernel(const SgdParams P) {
   const int lg = P.ring_log2[q];
   const uint32_t qmask = (1u << lg) - 1u;
   const unsigned long long* ring_q = P.ring + P.ring_base[q];
-  float4* __restrict__ W4 = reinterpret_cast<float4*>(P.W);
-  float4* __restrict__ H4 = reinterpret_cast<float4*>(P.H);
+  chunk_t* __restrict__ W4 = reinterpret_cast<chunk_t*>(P.W);
+  chunk_t* __restrict__ H4 = reinterpret_cast<chunk_t*>(P.H);
   const int64_t pitch4 = P.pitch >> 2;
   const int k4 = P.k4;
   const float lam = P.lambda;
@@ -181,7 +219,10 @@ nomad_batched_kernel(const SgdParams P) {
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
-        if (idx < k4) cp_async16(hbuf + (r * CPL + cc) * 32 + lane, H4 + jr * pitch4 + idx);
+        if (idx < k4) {
+          if constexpr (BF) cp_async8(hbuf + (r * CPL + cc) * 32 + lane, H4 + jr * pitch4 + idx);
+          else cp_async16(hbuf + (r * CPL + cc) * 32 + lane, H4 + jr * pitch4 + idx);
+        }
       }
     }
     int loaded = T < kRecInit ? T : kRecInit;
@@ -225,8 +266,10 @@ nomad_batched_kernel(const SgdParams P) {
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc) {
           const int idx = lane + 32 * cc;
-          if (idx < k4)
-            cp_async16(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
+          if (idx < k4) {
+            if constexpr (BF) cp_async8(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
+            else cp_async16(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
+          }
         }
       }
       if (lane == slot) {
@@ -263,7 +306,7 @@ nomad_batched_kernel(const SgdParams P) {
         s = __shfl_sync(kFull, s_tok, vlane);
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc)  // lanes past k/4 hold zeros, never smem
-          h[cc] = lane + 32 * cc < k4 ? hbuf[(k * CPL + cc) * 32 + lane]
+          h[cc] = lane + 32 * cc < k4 ? Storage<BF>::widen(hbuf[(k * CPL + cc) * 32 + lane])
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
         if (DEBUG && lane == 0) {
           const uint32_t tk = atomicAdd(P.log_ticket, 1u);
@@ -294,13 +337,14 @@ nomad_batched_kernel(const SgdParams P) {
       const int2 rc = recs[t % kRecBuf];
       const int slot = t % R;
       const int direct = __shfl_sync(kFull, dflag, slot);
-      float4* wrow = W4 + int64_t(rc.x) * pitch4;
+      chunk_t* wrow = W4 + int64_t(rc.x) * pitch4;
       float4 w[CPL];
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
         w[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < k4) w[cc] = direct ? __ldcg(wrow + idx) : rows[(slot * CPL + cc) * 32 + lane];
+        if (idx < k4)
+          w[cc] = Storage<BF>::widen(direct ? __ldcg(wrow + idx) : rows[(slot * CPL + cc) * 32 + lane]);
       }
       float part = 0.f;
 #pragma unroll
@@ -324,7 +368,16 @@ nomad_batched_kernel(const SgdParams P) {
         hn.z = fmaf(s, fmaf(err, w[cc].z, -lam * h[cc].z), h[cc].z);
         hn.w = fmaf(s, fmaf(err, w[cc].w, -lam * h[cc].w), h[cc].w);
         if (idx < k4) {
-          wrow[idx] = wn;
+          if constexpr (BF) {
+            const int64_t rix = vbeg + (t - vsoff);
+            const uint4 rb = philox4x32_10(
+                make_uint4(uint32_t(rix), uint32_t(uint64_t(rix) >> 32), uint32_t(meta_a[k].z),
+                           0x57000000u | uint32_t(idx)),
+                seed);
+            wrow[idx] = pack_sr(wn, rb.x, rb.y);
+          } else {
+            wrow[idx] = wn;
+          }
           h[cc] = hn;
         }
       }
@@ -335,7 +388,16 @@ nomad_batched_kernel(const SgdParams P) {
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc) {
           const int idx = lane + 32 * cc;
-          if (idx < k4) __stcg(H4 + int64_t(jv) * pitch4 + idx, h[cc]);
+          if (idx < k4) {
+            if constexpr (BF) {
+              const uint4 rb = philox4x32_10(
+                  make_uint4(uint32_t(vseg), uint32_t(meta_a[k].z), 0u, 0x48000000u | uint32_t(idx)),
+                  seed);
+              __stcg(H4 + int64_t(jv) * pitch4 + idx, pack_sr(h[cc], rb.z, rb.w));
+            } else {
+              __stcg(H4 + int64_t(jv) * pitch4 + idx, h[cc]);
+            }
+          }
         }
         if (vend - vsoff >= kHeavy) {  // long visit: hand the token on now
           if (lane == vlane) {
@@ -367,28 +429,23 @@ nomad_batched_kernel(const SgdParams P) {
   }
 }
 
-template <int CPL>
-const void* batched_ptr(bool debug) {
-  return debug ? (const void*)nomad_batched_kernel<CPL, true>
-               : (const void*)nomad_batched_kernel<CPL, false>;
+template <int CPL, bool BF>
+const void* batched_ptr(bool debug, size_t* smem_per_warp) {
+  *smem_per_warp = size_t(warp_smem_bytes<CPL, BF>());
+  return debug ? (const void*)nomad_batched_kernel<CPL, BF, true>
+               : (const void*)nomad_batched_kernel<CPL, BF, false>;
 }
 
 }  // namespace
 
 // Kernel pointer and per-warp shared memory (bytes) of the batched kernel.
-const void* batched_kernel(int k4, bool debug, size_t* smem_per_warp) {
-  if (k4 <= 32) {
-    *smem_per_warp = sizeof(float4) * warp_smem_f4<1>();
-    return batched_ptr<1>(debug);
-  }
-  if (k4 <= 64) {
-    *smem_per_warp = sizeof(float4) * warp_smem_f4<2>();
-    return batched_ptr<2>(debug);
-  }
-  if (k4 <= 128) {
-    *smem_per_warp = sizeof(float4) * warp_smem_f4<4>();
-    return batched_ptr<4>(debug);
-  }
+const void* batched_kernel(int k4, bool debug, bool bf16, size_t* smem_per_warp) {
+  if (k4 <= 32) return bf16 ? batched_ptr<1, true>(debug, smem_per_warp)
+                            : batched_ptr<1, false>(debug, smem_per_warp);
+  if (k4 <= 64) return bf16 ? batched_ptr<2, true>(debug, smem_per_warp)
+                            : batched_ptr<2, false>(debug, smem_per_warp);
+  if (k4 <= 128) return bf16 ? batched_ptr<4, true>(debug, smem_per_warp)
+                             : batched_ptr<4, false>(debug, smem_per_warp);
   return nullptr;
 }
 

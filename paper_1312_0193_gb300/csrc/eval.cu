@@ -19,9 +19,26 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kEvalThreads = 256;
+
+// bfloat16 (upper half of a binary32): widening is exact; narrowing rounds to
+// nearest, ties to even (initial values and factors set by the caller).
+__device__ __forceinline__ uint32_t bf16_rn(float x) {
+  const uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (u >> 16) | ((u & 0x007fffffu) ? 0x40u : 0u);
+  return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float4 widen4(uint2 c) {
+  return make_float4(__uint_as_float(c.x << 16), __uint_as_float(c.x & 0xffff0000u),
+                     __uint_as_float(c.y << 16), __uint_as_float(c.y & 0xffff0000u));
+}
+__device__ __forceinline__ float4 widen4(float4 c) { return c; }
+__device__ __forceinline__ uint2 narrow4(float4 v) {
+  return make_uint2(bf16_rn(v.x) | (bf16_rn(v.y) << 16), bf16_rn(v.z) | (bf16_rn(v.w) << 16));
+}
 constexpr int kEvalBlocksPerSm = 8;
 
-__global__ void init_factor_kernel(float4* __restrict__ F, int64_t rows, int32_t k,
+template <typename C>
+__global__ void init_factor_kernel(C* __restrict__ F, int64_t rows, int32_t k,
                                    int32_t k4, int64_t pitch4, float c,
                                    uint32_t which, uint2 seed) {
   const int64_t total = rows * k4;
@@ -38,7 +55,9 @@ __global__ void init_factor_kernel(float4* __restrict__ F, int64_t rows, int32_t
       const float u = float(words[i] >> 8) * (1.0f / 16777216.0f);  // exact
       v[i] = (4 * ch + i < k) ? __fmul_rn(u, c) : 0.0f;
     }
-    F[r * pitch4 + ch] = make_float4(v[0], v[1], v[2], v[3]);
+    const float4 c4 = make_float4(v[0], v[1], v[2], v[3]);
+    if constexpr (sizeof(C) == 16) F[r * pitch4 + ch] = c4;
+    else F[r * pitch4 + ch] = narrow4(c4);
   }
 }
 
@@ -62,8 +81,9 @@ __device__ __forceinline__ void block_store_sum(double acc, double* __restrict__
   }
 }
 
+template <typename C>
 __global__ void __launch_bounds__(kEvalThreads)
-sq_error_kernel(const float4* __restrict__ W4, const float4* __restrict__ H4,
+sq_error_kernel(const C* __restrict__ W4, const C* __restrict__ H4,
                 int64_t pitch4, int32_t k4, int32_t G, const int32_t* __restrict__ rows,
                 const int32_t* __restrict__ cols, const float* __restrict__ vals,
                 int64_t nnz, int64_t m, int64_t n, int32_t* __restrict__ status,
@@ -86,7 +106,7 @@ sq_error_kernel(const float4* __restrict__ W4, const float4* __restrict__ H4,
     }
     float part = 0.f;
     for (int ch = sub; ch < k4; ch += G) {
-      const float4 w = W4[i * pitch4 + ch], h = H4[j * pitch4 + ch];
+      const float4 w = widen4(W4[i * pitch4 + ch]), h = widen4(H4[j * pitch4 + ch]);
       part = fmaf(w.x, h.x, part);
       part = fmaf(w.y, h.y, part);
       part = fmaf(w.z, h.z, part);
@@ -103,8 +123,9 @@ sq_error_kernel(const float4* __restrict__ W4, const float4* __restrict__ H4,
 
 // J over the loaded training ratings, visiting segment by segment so that
 // h_j of the segment's item is known.
+template <typename C>
 __global__ void __launch_bounds__(kEvalThreads)
-objective_kernel(const float4* __restrict__ W4, const float4* __restrict__ H4,
+objective_kernel(const C* __restrict__ W4, const C* __restrict__ H4,
                  int64_t pitch4, int32_t k4, const int2* __restrict__ rec,
                  const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_col,
                  int64_t n_seg, float lambda, double* __restrict__ partials) {
@@ -116,7 +137,7 @@ objective_kernel(const float4* __restrict__ W4, const float4* __restrict__ H4,
     const int64_t j = seg_col[s];
     float hh = 0.f;
     for (int ch = lane; ch < k4; ch += 32) {
-      const float4 h = H4[j * pitch4 + ch];
+      const float4 h = widen4(H4[j * pitch4 + ch]);
       hh = fmaf(h.x, h.x, fmaf(h.y, h.y, fmaf(h.z, h.z, fmaf(h.w, h.w, hh))));
     }
     hh = group_sum(hh, 32);
@@ -125,7 +146,7 @@ objective_kernel(const float4* __restrict__ W4, const float4* __restrict__ H4,
       const int64_t i = rc.x;
       float dot = 0.f, ww = 0.f;
       for (int ch = lane; ch < k4; ch += 32) {
-        const float4 w = W4[i * pitch4 + ch], h = H4[j * pitch4 + ch];
+        const float4 w = widen4(W4[i * pitch4 + ch]), h = widen4(H4[j * pitch4 + ch]);
         dot = fmaf(w.x, h.x, fmaf(w.y, h.y, fmaf(w.z, h.z, fmaf(w.w, h.w, dot))));
         ww = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, ww))));
       }
@@ -154,6 +175,26 @@ __global__ void sum_partials(const double* __restrict__ partials, int n,
   }
 }
 
+__global__ void bf16_rows_to_f32(const uint16_t* __restrict__ src, int64_t rows, int32_t k,
+                                 int32_t pitch, float* __restrict__ dst) {
+  const int64_t total = rows * k;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int64_t r = t / k, l = t - r * k;
+    dst[t] = __uint_as_float(uint32_t(src[r * pitch + l]) << 16);
+  }
+}
+
+__global__ void f32_rows_to_bf16(const float* __restrict__ src, int64_t rows, int32_t k,
+                                 int32_t pitch, uint16_t* __restrict__ dst) {
+  const int64_t total = rows * int64_t(pitch);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int64_t r = t / pitch, l = t - r * pitch;
+    dst[t] = l < k ? uint16_t(bf16_rn(src[r * k + l])) : uint16_t(0);
+  }
+}
+
 int eval_grid(nomad_handle* h) {
   int g = h->sm_count * kEvalBlocksPerSm;
   return g > 0 ? g : 1;
@@ -177,10 +218,17 @@ int init_factors(nomad_handle* h, cudaStream_t st) {
   const uint2 seed = make_uint2(uint32_t(h->sched.seed), uint32_t(h->sched.seed >> 32));
   const int64_t pitch4 = h->pitch / 4;
   const int grid = eval_grid(h);
-  init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<float4*>(h->W), h->m, h->k,
-                                                   h->k4, pitch4, c, kTagInitW, seed);
-  init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<float4*>(h->H), h->n, h->k,
-                                                   h->k4, pitch4, c, kTagInitH, seed);
+  if (h->elem == 2) {
+    init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<uint2*>(h->W), h->m, h->k,
+                                                     h->k4, pitch4, c, kTagInitW, seed);
+    init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<uint2*>(h->H), h->n, h->k,
+                                                     h->k4, pitch4, c, kTagInitH, seed);
+  } else {
+    init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<float4*>(h->W), h->m, h->k,
+                                                     h->k4, pitch4, c, kTagInitW, seed);
+    init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<float4*>(h->H), h->n, h->k,
+                                                     h->k4, pitch4, c, kTagInitH, seed);
+  }
   h->launches += 2;
   return cudaGetLastError() == cudaSuccess ? NOMAD_OK : NOMAD_ERR_CUDA;
 }
@@ -191,9 +239,14 @@ int rmse_sum(nomad_handle* h, int64_t nnz, const int32_t* d_rows, const int32_t*
   if (int rc = ensure_partials(h, grid)) return rc;
   int G = 1;
   while (G < h->k4 && G < 32) G <<= 1;
-  sq_error_kernel<<<grid, kEvalThreads, 0, st>>>(
-      static_cast<const float4*>(h->W), static_cast<const float4*>(h->H), h->pitch / 4, h->k4,
-      G, d_rows, d_cols, d_vals, nnz, h->m, h->n, h->status, h->partials);
+  if (h->elem == 2)
+    sq_error_kernel<<<grid, kEvalThreads, 0, st>>>(
+        static_cast<const uint2*>(h->W), static_cast<const uint2*>(h->H), h->pitch / 4, h->k4,
+        G, d_rows, d_cols, d_vals, nnz, h->m, h->n, h->status, h->partials);
+  else
+    sq_error_kernel<<<grid, kEvalThreads, 0, st>>>(
+        static_cast<const float4*>(h->W), static_cast<const float4*>(h->H), h->pitch / 4, h->k4,
+        G, d_rows, d_cols, d_vals, nnz, h->m, h->n, h->status, h->partials);
   sum_partials<<<1, 256, 0, st>>>(h->partials, grid, h->result);
   h->launches += 2;
   if (cudaMemcpyAsync(out, h->result, sizeof(double), cudaMemcpyDeviceToHost, st) !=
@@ -205,9 +258,14 @@ int rmse_sum(nomad_handle* h, int64_t nnz, const int32_t* d_rows, const int32_t*
 int objective_sum(nomad_handle* h, double* out, cudaStream_t st) {
   const int grid = eval_grid(h);
   if (int rc = ensure_partials(h, grid)) return rc;
-  objective_kernel<<<grid, kEvalThreads, 0, st>>>(
-      static_cast<const float4*>(h->W), static_cast<const float4*>(h->H), h->pitch / 4, h->k4,
-      h->rec, h->seg_ptr, h->seg_col, h->n_seg, h->lambda, h->partials);
+  if (h->elem == 2)
+    objective_kernel<<<grid, kEvalThreads, 0, st>>>(
+        static_cast<const uint2*>(h->W), static_cast<const uint2*>(h->H), h->pitch / 4, h->k4,
+        h->rec, h->seg_ptr, h->seg_col, h->n_seg, h->lambda, h->partials);
+  else
+    objective_kernel<<<grid, kEvalThreads, 0, st>>>(
+        static_cast<const float4*>(h->W), static_cast<const float4*>(h->H), h->pitch / 4, h->k4,
+        h->rec, h->seg_ptr, h->seg_col, h->n_seg, h->lambda, h->partials);
   sum_partials<<<1, 256, 0, st>>>(h->partials, grid, h->result);
   h->launches += 2;
   if (cudaMemcpyAsync(out, h->result, sizeof(double), cudaMemcpyDeviceToHost, st) !=
@@ -219,6 +277,12 @@ int objective_sum(nomad_handle* h, double* out, cudaStream_t st) {
 int factors_to_f32(nomad_handle* h, int which, float* d_dense, cudaStream_t st) {
   const int64_t rows = which == 0 ? h->m : h->n;
   const void* src = which == 0 ? h->W : h->H;
+  if (h->elem == 2) {
+    bf16_rows_to_f32<<<eval_grid(h), kEvalThreads, 0, st>>>(static_cast<const uint16_t*>(src),
+                                                           rows, h->k, h->pitch, d_dense);
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? NOMAD_OK : NOMAD_ERR_CUDA;
+  }
   const cudaError_t e =
       cudaMemcpy2DAsync(d_dense, sizeof(float) * h->k, src, sizeof(float) * h->pitch,
                         sizeof(float) * h->k, rows, cudaMemcpyDeviceToDevice, st);
@@ -228,6 +292,12 @@ int factors_to_f32(nomad_handle* h, int which, float* d_dense, cudaStream_t st) 
 int factors_from_f32(nomad_handle* h, int which, const float* d_dense, cudaStream_t st) {
   const int64_t rows = which == 0 ? h->m : h->n;
   void* dst = which == 0 ? h->W : h->H;
+  if (h->elem == 2) {
+    f32_rows_to_bf16<<<eval_grid(h), kEvalThreads, 0, st>>>(d_dense, rows, h->k, h->pitch,
+                                                           static_cast<uint16_t*>(dst));
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? NOMAD_OK : NOMAD_ERR_CUDA;
+  }
   const cudaError_t e =
       cudaMemcpy2DAsync(dst, sizeof(float) * h->pitch, d_dense, sizeof(float) * h->k,
                         sizeof(float) * h->k, rows, cudaMemcpyDeviceToDevice, st);

@@ -193,7 +193,10 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
       sched.n_workers < 0 || sched.warps_per_block < 0 || sched.spin_timeout_ns < 0 ||
       (sched.variant != NOMAD_VARIANT_BATCHED && sched.variant != NOMAD_VARIANT_SIMPLE))
     return NOMAD_ERR_INVALID_ARG;
-  if (sched.precision != NOMAD_FP32) return NOMAD_ERR_UNSUPPORTED;
+  if (sched.precision != NOMAD_FP32 && sched.precision != NOMAD_BF16) return NOMAD_ERR_INVALID_ARG;
+  if (sched.precision == NOMAD_BF16 &&
+      (sched.mode != NOMAD_MODE_EPOCH || sched.variant != NOMAD_VARIANT_BATCHED))
+    return NOMAD_ERR_UNSUPPORTED;  // bfloat16 storage: batched epoch-mode kernel only
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || sched.device < 0 || sched.device >= ndev) {
     cudaGetLastError();
@@ -207,6 +210,7 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
   h->k4 = (k + 3) / 4;
   h->pitch = h->k4 * 4;
   h->lambda = lambda;
+  h->elem = sched.precision == NOMAD_BF16 ? 2 : 4;
   h->sched = sched;
   h->device = sched.device;
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
@@ -226,7 +230,7 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
   }
   h->blocks = (h->p + h->warps_per_block - 1) / h->warps_per_block;
 
-  const size_t esz = sizeof(float);
+  const size_t esz = size_t(h->elem);
   void* vp = nullptr;
   cudaError_t e;
   if ((e = dev_alloc(h, &vp, esz * size_t(m) * h->pitch)) != cudaSuccess) goto oom;

@@ -134,6 +134,7 @@ struct DeviceBuf {
 struct nomad_handle {
   int64_t m = 0, n = 0;
   int32_t k = 0, k4 = 0, pitch = 0;
+  int32_t elem = 4;                // bytes per stored entry of W, H
   float lambda = 0.f;
   nomad_schedule sched{};
   int device = 0;
@@ -208,7 +209,7 @@ int max_resident_workers(int device, int warps_per_block, int k4, int precision,
 int default_warps_per_block();
 // Batched epoch-mode worker kernel (epoch_batched.cu): pointer and dynamic
 // shared memory per warp in bytes; nullptr for an unsupported k4.
-const void* batched_kernel(int k4, bool debug, size_t* smem_per_warp);
+const void* batched_kernel(int k4, bool debug, bool bf16, size_t* smem_per_warp);
 
 // Initialisation, evaluation and factor copies (eval.cu).
 int init_factors(nomad_handle* h, cudaStream_t stream);

@@ -341,10 +341,12 @@ const void* epoch_kernel_ptr(bool debug, int mode) {
 
 // The worker kernel for a handle's settings and its dynamic shared memory per
 // warp (bytes).
-const void* worker_kernel(int k4, bool debug, int mode, int variant, size_t* smem_per_warp) {
+const void* worker_kernel(int k4, bool debug, int mode, int variant, int precision,
+                          size_t* smem_per_warp) {
   *smem_per_warp = 0;
   if (mode == NOMAD_MODE_EPOCH && variant == NOMAD_VARIANT_BATCHED)
-    return batched_kernel(k4, debug, smem_per_warp);
+    return batched_kernel(k4, debug, precision == NOMAD_BF16, smem_per_warp);
+  if (precision != NOMAD_FP32) return nullptr;  // bfloat16 storage: batched kernel only
   if (k4 <= 32) return epoch_kernel_ptr<1>(debug, mode);
   if (k4 <= 64) return epoch_kernel_ptr<2>(debug, mode);
   if (k4 <= 128) return epoch_kernel_ptr<4>(debug, mode);
@@ -353,14 +355,13 @@ const void* worker_kernel(int k4, bool debug, int mode, int variant, size_t* sme
 
 int max_resident_workers(int device, int warps_per_block, int k4, int precision, int mode,
                          int variant, int* blocks_per_sm) {
-  (void)precision;
   if (warps_per_block <= 0) warps_per_block = kDefaultWarpsPerBlock;
   if (warps_per_block > kMaxWarpsPerBlock) return -1;
   int per_sm = 1 << 30;
   // the debug variant must fit the same grid
   for (int dbg = 0; dbg < 2; ++dbg) {
     size_t spw = 0;
-    const void* fn = worker_kernel(k4, dbg, mode, variant, &spw);
+    const void* fn = worker_kernel(k4, dbg, mode, variant, precision, &spw);
     if (!fn) return -1;
     const size_t smem = spw * warps_per_block;
     if (smem > 48 * 1024 &&
@@ -448,7 +449,8 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   if (h->nnz == 0) return NOMAD_OK;
 
   size_t spw = 0;
-  const void* fn = worker_kernel(h->k4, debug, h->sched.mode, h->sched.variant, &spw);
+  const void* fn = worker_kernel(h->k4, debug, h->sched.mode, h->sched.variant,
+                                 h->sched.precision, &spw);
   const size_t smem = spw * size_t(h->warps_per_block);
   void* args[] = {&P};
   if (!h->ev_start) {

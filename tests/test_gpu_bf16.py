@@ -1,0 +1,116 @@
+"""bfloat16 storage of W and H on the GPU (binary32 arithmetic, stochastic
+rounding on write-back) against the oracle's bfloat16 replay.
+
+Tolerance of the replay comparison.  Both sides take the same stochastic
+rounding draws (same Philox counters), but the binary32 values they round
+differ by a few units in the last place (the GPU sums the dot product as a
+lane tree and fuses multiply-adds; the oracle sums left to right).  A
+difference below one bfloat16 step still flips a rounding decision with
+probability |difference| / step, i.e. about 2^-16 per written value; a flip
+moves that value by one bfloat16 step (2^-8 relative) and later updates
+carry it.  On the tiny problem this leaves a relative L2 distance of order
+1e-3; 1e-2 is the bound used.  The same run agrees to about 1e-6 in binary32.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1312_0193_gb300 import Nomad, NomadError  # noqa: E402
+from paper_1312_0193_gb300 import nomad as nb  # noqa: E402
+
+BF16_REPLAY_TOL = 1e-2
+REDUCE_TOL = 1e-6
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make(r, k, lam, **kw):
+    nm = Nomad(r.m, r.n, k, lam, precision="bf16", **kw)
+    nm.load_coo(r.train_rows.cuda(), r.train_cols.cuda(), r.train_vals.cuda())
+    return nm
+
+
+@pytest.mark.parametrize("k,seed", [(10, 2), (100, 7), (130, 5)])
+def test_bf16_init_bit_exact(k, seed):
+    with Nomad(300, 170, k, 0.05, seed=seed, precision="bf16") as nm:
+        W, H = nm.factors()
+    for F, rows, which in ((W, 300, 0), (H, 170, 1)):
+        want = oracle.bf16_to_f32(
+            oracle.bf16_rn(oracle.init_factor(rows, k, seed, which).astype(np.float32)))
+        assert np.array_equal(F, want)
+
+
+def test_bf16_only_with_batched_epoch_kernel():
+    with pytest.raises(NomadError) as e:
+        Nomad(10, 10, 4, 0.1, precision="bf16", variant="simple")
+    assert e.value.code == nb.NOMAD_ERR_UNSUPPORTED
+    with pytest.raises(NomadError):
+        Nomad(10, 10, 4, 0.1, precision="bf16", mode="uniform")
+
+
+@pytest.mark.parametrize("k,p,epochs,alpha", [(10, 64, 10, 0.05), (100, 40, 2, 0.01)])
+def test_bf16_replay(k, p, epochs, alpha):
+    r = synth.tiny_planted(1) if k == 10 else synth.netflix_shaped(0.0005, seed=3)
+    tr, tc, tv, *_ = r.numpy()
+    lam, beta, seed = 0.05, 0.05, 11
+    with make(r, k, lam, alpha=alpha, beta=beta, debug=True, n_workers=p, seed=seed) as nm:
+        rw = oracle.partition_rows(r.m, tr, p)
+        L = oracle.build_layout(r.m, r.n, tr, tc, tv, rw, p)
+        W0, H0 = nm.factors()
+        nm.epoch(epochs)
+        nm.check()
+        seg, ep = nm.replay_log()
+        Wg, Hg = nm.factors()
+        counts, viol = nm.debug_counts()
+    assert viol == 0 and np.all(counts == epochs)
+    Wb, Hb, cnt = oracle.replay_bf16(L, seg, ep, oracle.bf16_rn(W0), oracle.bf16_rn(H0),
+                                     float(np.float32(lam)), float(np.float32(alpha)),
+                                     float(np.float32(beta)), seed)
+    assert np.array_equal(cnt, counts)
+    Wo, Ho = oracle.bf16_to_f32(Wb), oracle.bf16_to_f32(Hb)
+    # every stored value is a bfloat16
+    assert np.array_equal(Wg, oracle.bf16_to_f32(oracle.bf16_rn(Wg)))
+    assert rel(Wg, Wo) < BF16_REPLAY_TOL and rel(Hg, Ho) < BF16_REPLAY_TOL, (rel(Wg, Wo), rel(Hg, Ho))
+
+
+def test_bf16_factors_roundtrip_and_rmse():
+    r = synth.tiny_planted(1)
+    tr, tc, tv, er, ec, ev = r.numpy()
+    rng = np.random.default_rng(4)
+    W = rng.normal(size=(r.m, 10)).astype(np.float32)
+    H = rng.normal(size=(r.n, 10)).astype(np.float32)
+    with make(r, 10, 0.05) as nm:
+        nm.set_factors(W, H)
+        W2, H2 = nm.factors()
+        got = nm.rmse(er, ec, ev)
+        J = nm.objective()
+    assert np.array_equal(W2, oracle.bf16_to_f32(oracle.bf16_rn(W)))
+    assert np.array_equal(H2, oracle.bf16_to_f32(oracle.bf16_rn(H)))
+    want = oracle.rmse(er, ec, ev, W2.astype(np.float64), H2.astype(np.float64))
+    assert abs(got - want) <= REDUCE_TOL * want
+    Jw = oracle.objective(tr, tc, tv, W2.astype(np.float64), H2.astype(np.float64),
+                          float(np.float32(0.05)))
+    assert abs(J - Jw) <= REDUCE_TOL * Jw
+
+
+def test_bf16_free_run_quality_close_to_fp32():
+    """20 epochs at the paper's schedule: the bfloat16 run's test RMSE is
+    within 0.5% of the binary32 run's."""
+    r = synth.tiny_planted(1)
+    er, ec, ev = r.numpy()[3:]
+    out = {}
+    for prec in ("fp32", "bf16"):
+        with Nomad(r.m, r.n, 10, 0.05, precision=prec) as nm:
+            nm.load_coo(r.train_rows.cuda(), r.train_cols.cuda(), r.train_vals.cuda())
+            nm.epoch(20)
+            out[prec] = nm.rmse(er, ec, ev)
+    assert abs(out["bf16"] - out["fp32"]) <= 0.005 * out["fp32"], out
