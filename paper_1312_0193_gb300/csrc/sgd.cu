@@ -88,8 +88,13 @@ __device__ __forceinline__ void sgd_segment(float4 (&h)[CPL], float4* __restrict
           float e = a - warp_sum(part);
           float step = s;
           if (COUNT) {
-            // uniform mode: s_t from the per-rating update counter t
-            const int t = rec_count[base + u];
+            // uniform mode: s_t from the per-rating update counter t.  Lane 0
+            // alone reads it (it also increments it below) and broadcasts:
+            // lanes of a warp need not run in lockstep, so a read by another
+            // lane could see the increment.
+            int t = 0;
+            if (lane == 0) t = rec_count[base + u];
+            t = __shfl_sync(kFull, t, 0);
             const float tf = float(t);
             step = P->alpha / (1.f + P->beta * tf * sqrtf(tf));
           }
@@ -275,6 +280,7 @@ nomad_uniform_kernel(const SgdParams P) {
       const unsigned hit = __ballot_sync(kFull, sg >= 0 && __ldg(P.seg_worker + sg) == q);
       if (hit) seg = __shfl_sync(kFull, sg, __ffs(hit) - 1);
     }
+    __syncwarp();
     if (DEBUG && lane == 0) {
       const uint32_t t = atomicAdd(P.log_ticket, 1u);
       if (int64_t(t) < P.log_cap) {

@@ -297,3 +297,33 @@ def test_free_run_large_steps_within_order_spread(tiny):
         runs.append(oracle.rmse(er, ec, ev, Wo, Ho))
     mu, sd = float(np.mean(runs)), float(np.std(runs))
     assert abs(g - mu) <= 3 * sd + 0.005 * mu, (g, mu, sd)
+
+
+# ---------------------------------------------------------------- uniform mode
+@pytest.mark.parametrize("p", [16, 64])
+def test_uniform_mode_replay_and_budget(tiny, p):
+    """Alg. 1 literally: the next worker is uniform over all p, a visit to a
+    worker without ratings of the item applies nothing, the per-rating update
+    count gives t, and a call stops after n_epochs * nnz updates.  The logged
+    order of non-empty visits replays to the same factors on the oracle."""
+    tr, tc, tv, *_ = tiny.numpy()
+    a32, b32, lam32 = (float(np.float32(x)) for x in (0.05, 0.05, 0.05))
+    with make(tiny, 10, 0.05, alpha=0.05, beta=0.05, mode="uniform", debug=True,
+              n_workers=p) as nm:
+        L, _ = oracle_layout(nm, tiny)
+        W0, H0 = nm.factors()
+        nm.epoch(2)
+        nm.check()
+        seg, item = nm.replay_log()
+        Wg, Hg = nm.factors()
+        counts, viol = nm.debug_counts()
+    assert viol == 0
+    total = int(counts.sum())
+    assert 2 * tiny.nnz <= total <= 2 * tiny.nnz + p * int(np.diff(L["seg_ptr"]).max())
+    real = seg[seg >= 0]
+    # every logged segment belongs to the logged item
+    assert np.array_equal(L["seg_col"][real], item[seg >= 0])
+    Wo, Ho, cnt = oracle.replay(L, real, W0, H0, lam32, a32, b32, precision="f32")
+    assert np.array_equal(cnt, counts)
+    assert rel(Wg, Wo) < REPLAY_TOL and rel(Hg, Ho) < REPLAY_TOL
+    assert seg.size > 5 * p  # many visits, some of them to workers without ratings
