@@ -117,6 +117,217 @@ __device__ __forceinline__ void load_records(int2* recs, const int2* __restrict_
   }
 }
 
+
+// Transposed warp reduction: v[0..31] are this lane's partial sums of 32
+// quantities; on return lane l holds the warp-wide sum of quantity l.  Each
+// level halves the values a lane keeps and exchanges the other half with the
+// partner lane, so the 32 sums take 31 shuffles that are mostly independent.
+__device__ __forceinline__ float warp_sum_transposed(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return v[0];
+}
+
+// The updates of one long visit (>= kHeavy ratings) of token j, the serial
+// chain through h_j that bounds an epoch for the items with most ratings.
+//
+// The visit applies the per-rating step of Eq. w_update / h_update to its
+// ratings u = 0, 1, ... in order.  The rows of one visit are distinct users,
+// so within a block of B consecutive ratings every w_u is read before it is
+// written and only h changes from one update to the next.  With
+// a = 1 - s*lambda the recurrence h_{u+1} = a h_u + s e_u w_u unrolls to
+//
+//   e_u = A_u - a^u <w_u, h_0> - s * sum_{v<u} a^(u-1-v) <w_u, w_v> e_v,
+//
+// so the block needs the B dot products <w_u, h_0> and the B(B-1)/2 dot
+// products <w_u, w_v> (one transposed reduction), a B-step scalar forward
+// substitution for e_0..e_{B-1}, and then the vector updates
+// w_u' = a w_u + s e_u h_u, h_{u+1} = a h_u + s e_u w_u.  In exact arithmetic
+// this is the sequential update; the dependent chain per rating shrinks from
+// a full warp reduction to one shuffle and one multiply-add.
+//
+// W rows come through the warp's shared-memory ring (`rows`, 16 chunk slots
+// per lane), LB blocks ahead with cp.async; each lane copies and reads only
+// its own chunk of a row.  Records are held in lane registers, three 32-record
+// chunks (lane i holds record i of a chunk).  Earlier stores of this warp
+// precede these loads in program order.
+template <int CPL, bool BF, bool DEBUG>
+__device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF>::chunk_t* rows,
+                                           typename Storage<BF>::chunk_t* W4, int64_t pitch4,
+                                           int k4, const int2* __restrict__ rec, int64_t beg,
+                                           int c, float s, float lam, int epoch, uint2 seed,
+                                           int lane, int32_t* rec_count) {
+  constexpr int B = CPL == 4 ? 4 : 7;
+  constexpr int NS = B + B * (B - 1) / 2;
+  static_assert(NS <= 32, "one transposed reduction per block");
+  constexpr int LB = (16 / CPL) / B;  // blocks of rows in flight
+  static_assert(LB >= 1 && LB <= 2, "row ring holds the blocks in flight");
+  using chunk_t = typename Storage<BF>::chunk_t;
+  const float al = 1.f - s * lam;
+  // lane u < B: a^u, and s a^(u-1-v) for v < u
+  float aD = 1.f;
+#pragma unroll
+  for (int i = 0; i < B - 1; ++i)
+    if (i < lane) aD *= al;
+  float cg[B - 1];
+#pragma unroll
+  for (int v = 0; v < B - 1; ++v) {
+    float x = s;
+#pragma unroll
+    for (int i = 0; i < B - 2; ++i)
+      if (i < lane - 1 - v) x *= al;
+    cg[v] = x;
+  }
+  const int2 z2 = make_int2(0, 0);
+  int2 r0 = lane < c ? __ldcs(rec + beg + lane) : z2;
+  int2 r1 = lane + 32 < c ? __ldcs(rec + beg + 32 + lane) : z2;
+  int2 r2 = lane + 64 < c ? __ldcs(rec + beg + 64 + lane) : z2;
+  int c0 = 0;  // record chunk held in r0
+  // row of position u (warp-uniform, in chunk c0 or c0 + 1)
+  auto row_at = [&](int u) {
+    const int src = (u >> 5) == c0 ? r0.x : r1.x;
+    return __shfl_sync(kFull, src, u & 31);
+  };
+  auto fetch = [&](int bb) {  // the rows of block bb, one commit group
+    const int set = LB == 2 ? (bb & 1) : 0;
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int u = bb * B + i;
+      const int row = row_at(u);
+      if (u < c) {
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+          const int idx = lane + 32 * cc;
+          if (idx < k4) {
+            chunk_t* dst = rows + ((set * B + i) * CPL + cc) * 32 + lane;
+            if constexpr (BF) cp_async8(dst, W4 + int64_t(row) * pitch4 + idx);
+            else cp_async16(dst, W4 + int64_t(row) * pitch4 + idx);
+          }
+        }
+      }
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int l = 0; l < LB; ++l) fetch(l);
+
+  const int nblk = (c + B - 1) / B;
+  for (int b = 0; b < nblk; ++b) {
+    if (((b * B) >> 5) != c0) {  // next record chunk
+      r0 = r1;
+      r1 = r2;
+      ++c0;
+      const int p2 = (c0 + 2) * 32 + lane;
+      r2 = p2 < c ? __ldcs(rec + beg + p2) : z2;
+    }
+    if constexpr (LB == 2) cp_wait<1>();
+    else cp_wait<0>();
+    const int set = LB == 2 ? (b & 1) : 0;
+    float4 w[B][CPL];
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc)
+        w[i][cc] = lane + 32 * cc < k4 && b * B + i < c
+                       ? Storage<BF>::widen(rows[((set * B + i) * CPL + cc) * 32 + lane])
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    // lane partials: slots 0..B-1 <w_u, h_0>, then <w_u, w_v> for v < u
+    float v[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = 0.f;
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        v[u] = fmaf(w[u][cc].x, h[cc].x, v[u]);
+        v[u] = fmaf(w[u][cc].y, h[cc].y, v[u]);
+        v[u] = fmaf(w[u][cc].z, h[cc].z, v[u]);
+        v[u] = fmaf(w[u][cc].w, h[cc].w, v[u]);
+      }
+#pragma unroll
+    for (int u = 1; u < B; ++u)
+#pragma unroll
+      for (int q = 0; q < u; ++q) {
+        const int t = B + u * (u - 1) / 2 + q;
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+          v[t] = fmaf(w[u][cc].x, w[q][cc].x, v[t]);
+          v[t] = fmaf(w[u][cc].y, w[q][cc].y, v[t]);
+          v[t] = fmaf(w[u][cc].z, w[q][cc].z, v[t]);
+          v[t] = fmaf(w[u][cc].w, w[q][cc].w, v[t]);
+        }
+      }
+    // the slots just read take the rows of block b + LB (the partials above
+    // consumed every value read from them)
+    fetch(b + LB);
+    const float red = warp_sum_transposed(v, lane);
+    // lane u < B: A_u - a^u <w_u, h_0>, then the forward substitution
+    float acc;
+    {
+      const int u = b * B + (lane < B ? lane : 0);
+      const int y0 = __shfl_sync(kFull, r0.y, u & 31);
+      const int y1 = __shfl_sync(kFull, r1.y, u & 31);
+      acc = __int_as_float((u >> 5) == c0 ? y0 : y1) - aD * red;
+    }
+    float gs[B - 1];
+#pragma unroll
+    for (int q = 0; q < B - 1; ++q) {
+      const int src = lane > q && lane < B ? B + lane * (lane - 1) / 2 + q : 0;
+      gs[q] = cg[q] * __shfl_sync(kFull, red, src);
+    }
+    float e[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      e[q] = __shfl_sync(kFull, acc, q);
+      if (q < B - 1 && lane > q) acc = fmaf(-gs[q], e[q], acc);
+    }
+    // vector updates in rating order
+    const int nu = c - b * B < B ? c - b * B : B;
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      if (i >= nu) break;
+      const int u = b * B + i;
+      const float se = s * e[i];
+      chunk_t* wrow = W4 + int64_t(row_at(u)) * pitch4;
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int idx = lane + 32 * cc;
+        float4 wn;
+        wn.x = fmaf(se, h[cc].x, al * w[i][cc].x);
+        wn.y = fmaf(se, h[cc].y, al * w[i][cc].y);
+        wn.z = fmaf(se, h[cc].z, al * w[i][cc].z);
+        wn.w = fmaf(se, h[cc].w, al * w[i][cc].w);
+        h[cc].x = fmaf(al, h[cc].x, se * w[i][cc].x);
+        h[cc].y = fmaf(al, h[cc].y, se * w[i][cc].y);
+        h[cc].z = fmaf(al, h[cc].z, se * w[i][cc].z);
+        h[cc].w = fmaf(al, h[cc].w, se * w[i][cc].w);
+        if (idx < k4) {
+          if constexpr (BF) {
+            const int64_t rix = beg + u;
+            const uint4 rb = philox4x32_10(
+                make_uint4(uint32_t(rix), uint32_t(uint64_t(rix) >> 32), uint32_t(epoch),
+                           0x57000000u | uint32_t(idx)),
+                seed);
+            wrow[idx] = pack_sr(wn, rb.x, rb.y);
+          } else {
+            wrow[idx] = wn;
+          }
+        }
+      }
+      if (DEBUG && lane == 0) rec_count[beg + u] += 1;
+    }
+  }
+  cp_wait<0>();
+}
+
 template <int CPL, bool BF, bool DEBUG>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
 nomad_batched_kernel(const SgdParams P) {
@@ -225,8 +436,13 @@ nomad_batched_kernel(const SgdParams P) {
         }
       }
     }
-    int loaded = T < kRecInit ? T : kRecInit;
-    for (int p0 = 0; p0 < loaded; p0 += 32)
+    // long visits (ranks 0 .. nhv-1) take stream positions [0, T0) and run
+    // first on their own path; the generic stream starts at T0
+    const int nhv = __popc(hv);
+    int T0 = 0;
+    for (int r = 0; r < nhv; ++r) T0 += meta_a[r].y;
+    int loaded = T - T0 < kRecInit ? T : T0 + kRecInit;
+    for (int p0 = T0; p0 < loaded; p0 += 32)
       load_records(recs, P.rec, meta_a, meta_b, nb, p0, loaded - p0 < 32 ? loaded - p0 : 32,
                    lane);
     cp_commit();
@@ -254,6 +470,55 @@ nomad_batched_kernel(const SgdParams P) {
     }
     cp_wait_all();
     __syncwarp();
+    int q2 = -1;
+    if (mine && nseg >= 0) q2 = __ldg(P.seg_worker + nseg);
+
+    // ---- 5h. the long visits
+    for (int kh = 0; kh < nhv; ++kh) {
+      const int4 ma = meta_a[kh];
+      const int4 mb = meta_b[kh];
+      const int vl = mb.z;
+      const int64_t vb = (int64_t(mb.y) << 32) | uint32_t(mb.x);
+      const float sv = __shfl_sync(kFull, s_tok, vl);
+      float4 hh[CPL];
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc)
+        hh[cc] = lane + 32 * cc < k4 ? Storage<BF>::widen(hbuf[(kh * CPL + cc) * 32 + lane])
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (DEBUG && lane == 0) {
+        const uint32_t tk = atomicAdd(P.log_ticket, 1u);
+        if (int64_t(tk) < P.log_cap) {
+          P.log_seg[tk] = ma.w;
+          P.log_epoch[tk] = ma.z;
+        }
+        if (atomicExch(P.owner + ma.x, q) != -1) flag_ownership(P, q, ma.x);
+      }
+      long_visit<CPL, BF, DEBUG>(hh, rows, W4, pitch4, k4, P.rec, vb, ma.y, sv, lam, ma.z, seed,
+                                 lane, P.rec_count);
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int idx = lane + 32 * cc;
+        if (idx < k4) {
+          if constexpr (BF) {
+            const uint4 rb = philox4x32_10(
+                make_uint4(uint32_t(ma.w), uint32_t(ma.z), 0u, 0x48000000u | uint32_t(idx)), seed);
+            __stcg(H4 + int64_t(ma.x) * pitch4 + idx, pack_sr(hh[cc], rb.z, rb.w));
+          } else {
+            __stcg(H4 + int64_t(ma.x) * pitch4 + idx, hh[cc]);
+          }
+        }
+      }
+      if (lane == vl) {
+        __stcg(P.tok_hop + j, nh);
+        __stcg(P.tok_epoch + j, ne);
+        if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
+      }
+      __syncwarp();
+      if (lane == vl && nseg >= 0) {
+        __threadfence();
+        push_token(P, q2, uint32_t(nseg));
+      }
+    }
 
     // ---- 5a. cold start of the row ring: positions 0 .. R-2
     int win = -1;  // lane L < R: row of the latest position p with p % R == L
@@ -279,21 +544,19 @@ nomad_batched_kernel(const SgdParams P) {
     };
     // one commit group per position: at tick t exactly R-1 groups are
     // younger than position t's group, so cp.async.wait_group R-1 suffices
-    for (int pp = 0; pp < R - 1; ++pp) {
+    for (int pp = T0; pp < T0 + R - 1; ++pp) {
       if (pp < T) prefetch(pp);
       cp_commit();
     }
-    int q2 = -1;
-    if (mine && nseg >= 0) q2 = __ldg(P.seg_worker + nseg);
 
     // ---- 5b. the stream
-    int k = -1, vend = 0, vsoff = 0, vlane = 0, vseg = 0;
+    int k = nhv - 1, vend = T0, vsoff = 0, vlane = 0, vseg = 0;
     int64_t vbeg = 0;
     float s = 0.f;
     float4 h[CPL];
 #pragma unroll
     for (int cc = 0; cc < CPL; ++cc) h[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int t = 0; t < T; ++t) {
+    for (int t = T0; t < T; ++t) {
       if (t == vend) {  // a visit starts
         ++k;
         const int4 ma = meta_a[k];
