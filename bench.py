@@ -147,11 +147,11 @@ def barrier(world):
 
 
 # ---------------------------------------------------------------- workloads
-def make_workload(cfg: str, device):
+def make_workload(cfg: str, device, scale: float = 1.0):
     import synth
     gen, k, lam, alpha, beta = CONFIGS[cfg]
     fn = getattr(synth, gen)
-    r = fn(device=device) if cfg == "tiny" else fn(1.0, device=device)
+    r = fn(device=device) if cfg == "tiny" else fn(scale, device=device)
     return r, k, lam, alpha, beta
 
 
@@ -195,7 +195,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    r, k, lam, alpha, beta = make_workload(args.config, dev)
+    r, k, lam, alpha, beta = make_workload(args.config, dev, args.scale)
     nnz = r.nnz
     nm = Nomad(r.m, r.n, k, lam, alpha=alpha, beta=beta, device=local,
                n_workers=args.workers, warps_per_block=args.warps_per_block,
@@ -263,7 +263,9 @@ def run_ours(args):
         try:
             with open(tr_path) as f:
                 tj = json.load(f)
-            if tj.get("config") == args.config and tj.get("kernel_rev") == kernel_rev():
+            if (tj.get("config") == args.config and tj.get("scale", 1.0) == args.scale
+                    and tj.get("precision", "fp32") == args.precision
+                    and tj.get("kernel_rev") == kernel_rev()):
                 traffic = tj.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
@@ -298,7 +300,7 @@ def run_ours(args):
                          "unit": "GB/s", "frac": achieved_gbs / peak, "traffic": traffic,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
                          if peak_src == "measured" else "fallback 6.8 TB/s",
-                         "kernel": "nomad_epoch_kernel", "kernel_ms": kern_avg_s * 1e3,
+                         "kernel": "nomad_batched_kernel", "kernel_ms": kern_avg_s * 1e3,
                          "bytes_per_update": bytes_per_update},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_units / e2e_t, "unit": UNIT,
@@ -317,10 +319,14 @@ def run_ours(args):
 
 
 def kernel_rev():
-    """Hash of the epoch kernel's source, to tie profile figures to code."""
+    """Hash of the batched worker kernel's sources, to tie profile figures
+    to the code they were taken from."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_1312_0193_gb300", "csrc", "sgd.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    hs = hashlib.sha256()
+    for name in ("epoch_batched.cu", "sgd_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1312_0193_gb300", "csrc", name), "rb") as f:
+            hs.update(f.read())
+    return hs.hexdigest()[:16]
 
 
 # ---------------------------------------------------------------- reference arm
@@ -331,7 +337,7 @@ def run_reference(args):
         return
     import torch
     dev = torch.device("cuda", local) if torch.cuda.is_available() else "cpu"
-    r, k, lam, alpha, beta = make_workload(args.config, dev)
+    r, k, lam, alpha, beta = make_workload(args.config, dev, args.scale)
     per_step = max(1, args.ref_sample)
     for _ in range(args.warmup):
         cpu_sample_run(r, k, lam, alpha, beta, per_step // 4)
@@ -365,6 +371,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="netflix")
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload (same shape) for profiler captures")
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)

@@ -51,27 +51,37 @@ __device__ __forceinline__ void push_token(const SgdParams& P, int q,
 // Lane 0 only.  Returns the payload at position `head` of worker q's ring,
 // or -1 when the wait gave up (another worker failed, the stop flag of
 // uniform mode was raised, or this wait exceeded the timeout, in which case
-// the status word records it).
+// the status word records it).  The slot is polled with relaxed loads (an
+// acquire load would also invalidate the SM's L1, which the working warps of
+// the SM use) and a backoff of up to kMaxSleepNs; the acquire is one fence
+// once the slot is seen ready.
+constexpr unsigned kMaxSleepNs = 512;
 __device__ int pop_token(const SgdParams& P, int q, uint32_t head, int lg,
                          const unsigned long long* ring_q) {
   const unsigned long long* slot = ring_q + (head & ((1u << lg) - 1u));
   const uint32_t lap = head >> lg;
-  unsigned long long v = ld_acquire_u64(slot);
-  if (uint32_t(v >> 32) == lap) return int(uint32_t(v));
+  unsigned long long v = ld_relaxed_u64(slot);
+  if (uint32_t(v >> 32) == lap) {
+    fence_acq_rel_gpu();
+    return int(uint32_t(v));
+  }
   const unsigned long long t0 = globaltimer_ns();
   const unsigned long long max_iters =
       static_cast<unsigned long long>(P.timeout_ns) / 16ull + (1ull << 20);
   unsigned ns = 32;
   for (unsigned long long it = 0; it < max_iters; ++it) {
-    v = ld_acquire_u64(slot);
-    if (uint32_t(v >> 32) == lap) return int(uint32_t(v));
+    v = ld_relaxed_u64(slot);
+    if (uint32_t(v >> 32) == lap) {
+      fence_acq_rel_gpu();
+      return int(uint32_t(v));
+    }
     if ((it & 15) == 15) {
       if (ld_relaxed_i32(P.status) != 0) return -1;
       if (P.stop != nullptr && ld_relaxed_i32(P.stop) != 0) return -1;
       if (globaltimer_ns() - t0 > static_cast<unsigned long long>(P.timeout_ns)) break;
     }
     __nanosleep(ns);
-    if (ns < 128) ns <<= 1;
+    if (ns < kMaxSleepNs) ns <<= 1;
   }
   if (atomicCAS(P.status, 0, NOMAD_ERR_TIMEOUT) == 0) {
     atomicExch(P.status + 1, q);
