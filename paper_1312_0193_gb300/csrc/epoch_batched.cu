@@ -36,9 +36,11 @@ constexpr int kRecBuf = 128;   // circular buffer of record positions
 constexpr int kRecInit = 64;   // positions loaded before the first row copy
 constexpr int kHeavy = 32;     // visits this long go first and are pushed at once
 
+constexpr int kRowChunks = 16;  // row-ring chunks per lane (16 bytes of binary32 each)
+
 template <int CPL>
 struct RowRing {
-  static constexpr int R = 16 / CPL;  // slots; R-1 rows in flight
+  static constexpr int R = kRowChunks / CPL;  // slots; R-1 rows in flight
 };
 
 // Storage of W and H: binary32 (a chunk of 4 entries is a float4) or
@@ -154,11 +156,11 @@ __device__ __forceinline__ float warp_sum_transposed(float (&v)[32], int lane) {
 // this is the sequential update; the dependent chain per rating shrinks from
 // a full warp reduction to one shuffle and one multiply-add.
 //
-// W rows come through the warp's shared-memory ring (`rows`, 16 chunk slots
-// per lane), LB blocks ahead with cp.async; each lane copies and reads only
-// its own chunk of a row.  Records are held in lane registers, three 32-record
-// chunks (lane i holds record i of a chunk).  Earlier stores of this warp
-// precede these loads in program order.
+// W rows come through the warp's shared-memory ring (`rows`, kRowChunks
+// chunk slots per lane), LB blocks ahead with cp.async; each lane copies and
+// reads only its own chunk of a row.  Records are held in lane registers,
+// three 32-record chunks (lane i holds record i of a chunk).  Earlier stores
+// of this warp precede these loads in program order.
 template <int CPL, bool BF, bool DEBUG>
 __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF>::chunk_t* rows,
                                            typename Storage<BF>::chunk_t* W4, int64_t pitch4,
@@ -168,8 +170,9 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
   constexpr int B = CPL == 4 ? 4 : 7;
   constexpr int NS = B + B * (B - 1) / 2;
   static_assert(NS <= 32, "one transposed reduction per block");
-  constexpr int LB = (16 / CPL) / B;  // blocks of rows in flight
-  static_assert(LB >= 1 && LB <= 2, "row ring holds the blocks in flight");
+  constexpr int LB = (kRowChunks / CPL) / B;  // blocks of rows in flight
+  // positions up to B*(b + LB) + B - 1 lie in record chunks c0 and c0 + 1
+  static_assert(LB >= 1 && B * (LB + 1) - 1 <= 32, "row ring holds the blocks in flight");
   using chunk_t = typename Storage<BF>::chunk_t;
   const float al = 1.f - s * lam;
   // lane u < B: a^u, and s a^(u-1-v) for v < u
@@ -190,14 +193,14 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
   int2 r0 = lane < c ? __ldcs(rec + beg + lane) : z2;
   int2 r1 = lane + 32 < c ? __ldcs(rec + beg + 32 + lane) : z2;
   int2 r2 = lane + 64 < c ? __ldcs(rec + beg + 64 + lane) : z2;
-  int c0 = 0;  // record chunk held in r0
+  int c0 = 0;  // record chunk held in r0; r1, r2 hold the next two
   // row of position u (warp-uniform, in chunk c0 or c0 + 1)
   auto row_at = [&](int u) {
     const int src = (u >> 5) == c0 ? r0.x : r1.x;
     return __shfl_sync(kFull, src, u & 31);
   };
   auto fetch = [&](int bb) {  // the rows of block bb, one commit group
-    const int set = LB == 2 ? (bb & 1) : 0;
+    const int set = int(unsigned(bb) % unsigned(LB));
 #pragma unroll
     for (int i = 0; i < B; ++i) {
       const int u = bb * B + i;
@@ -228,9 +231,8 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
       const int p2 = (c0 + 2) * 32 + lane;
       r2 = p2 < c ? __ldcs(rec + beg + p2) : z2;
     }
-    if constexpr (LB == 2) cp_wait<1>();
-    else cp_wait<0>();
-    const int set = LB == 2 ? (b & 1) : 0;
+    cp_wait<LB - 1>();
+    const int set = int(unsigned(b) % unsigned(LB));
     float4 w[B][CPL];
 #pragma unroll
     for (int i = 0; i < B; ++i)
@@ -513,11 +515,8 @@ nomad_batched_kernel(const SgdParams P) {
         __stcg(P.tok_epoch + j, ne);
         if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
       }
-      __syncwarp();
-      if (lane == vl && nseg >= 0) {
-        __threadfence();
-        push_token(P, q2, uint32_t(nseg));
-      }
+      __syncwarp();  // orders every lane's H stores before the release below
+      if (lane == vl && nseg >= 0) push_token(P, q2, uint32_t(nseg));
     }
 
     // ---- 5a. cold start of the row ring: positions 0 .. R-2
@@ -662,18 +661,6 @@ nomad_batched_kernel(const SgdParams P) {
             }
           }
         }
-        if (vend - vsoff >= kHeavy) {  // long visit: hand the token on now
-          if (lane == vlane) {
-            __stcg(P.tok_hop + j, nh);
-            __stcg(P.tok_epoch + j, ne);
-            if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
-          }
-          __syncwarp();
-          if (lane == vlane && nseg >= 0) {
-            __threadfence();
-            push_token(P, q2, uint32_t(nseg));
-          }
-        }
       }
     }
 
@@ -684,11 +671,8 @@ nomad_batched_kernel(const SgdParams P) {
       __stcg(P.tok_epoch + j, ne);
       if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
     }
-    __syncwarp();
-    if (__any_sync(kFull, late && nseg >= 0)) {
-      __threadfence();
-      if (late && nseg >= 0) push_token(P, q2, uint32_t(nseg));
-    }
+    __syncwarp();  // orders every lane's H stores before the releases below
+    if (late && nseg >= 0) push_token(P, q2, uint32_t(nseg));
   }
 }
 

@@ -40,6 +40,10 @@ __device__ __forceinline__ uint32_t itinerary_slot(uint32_t hop, uint32_t d,
   return hop;  // not reached: the orbit of hop returns to [0, d)
 }
 
+// Appends `payload` to worker q's ring.  The slot is written with a release
+// store: every write this thread performed or observed before it (the other
+// lanes' stores of h_j, ordered by a preceding __syncwarp) is visible to the
+// worker whose acquire reads the slot.
 __device__ __forceinline__ void push_token(const SgdParams& P, int q,
                                            uint32_t payload) {
   const uint32_t pos = atomicAdd(P.ring_tail + q, 1u);
