@@ -270,6 +270,10 @@ def run_ours(args):
         except Exception:
             traffic = None
 
+    ttt = None
+    if rank == 0 and world == 1 and not args.no_ttt:
+        ttt = time_to_target(args, dev, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         upd, secs, desc = cpu_sample_run(r, k, lam, alpha, beta, args.cpu_sample)
@@ -307,6 +311,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
                     "steps": e2e_steps,
                     "step": "load_ratings(pinned host COO) + epoch + rmse(pinned host)"},
+            "time_to_target": ttt,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "test_rmse_last": rmses[-1] if rmses else None,
@@ -316,6 +321,47 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def time_to_target(args, dev, local):
+    """Time to the oracle's test RMSE: the Netflix-shaped workload at
+    `--ttt-scale`, generated on the CPU from its seed exactly as the oracle's
+    target script did, from the same initial factors.  Target = 1.005 x the
+    binary64 oracle's test RMSE after E epochs (tests/golden/rmse_targets.json).
+    GPU time = sum of the epoch kernels' CUDA-event times until the test RMSE
+    reaches the target (RMSE evaluation excluded), for binary32 and bfloat16
+    storage."""
+    import torch
+    import synth
+    from paper_1312_0193_gb300 import Nomad
+    path = os.path.join(ROOT, "tests", "golden", "rmse_targets.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f).get("%s@%g" % (args.config, args.ttt_scale))
+    if not t:
+        return None
+    gen, k, lam, alpha, beta = CONFIGS[args.config]
+    r = getattr(synth, gen)(args.ttt_scale, device="cpu").to(dev)
+    E = int(t["epochs"])
+    target = 1.005 * float(t["test_rmse"][-1])
+    out = {"workload": r.name, "nnz_train": r.nnz, "oracle_epochs": E,
+           "oracle_test_rmse": float(t["test_rmse"][-1]), "target": target,
+           "max_epochs": 2 * E}
+    for prec in ("fp32", "bf16"):
+        nm = Nomad(r.m, r.n, k, lam, alpha=alpha, beta=beta, device=local, precision=prec,
+                   seed=int(t.get("init_seed", 1)))
+        nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
+        secs, ep, rm = 0.0, 0, float("inf")
+        while ep < 2 * E and not rm <= target:
+            nm.epoch(1)
+            secs += nm.last_epoch_kernel_ms() / 1e3
+            rm = nm.rmse(r.test_rows, r.test_cols, r.test_vals)
+            ep += 1
+        out[prec] = {"reached": bool(rm <= target), "epochs": ep, "seconds": secs,
+                     "test_rmse": rm}
+        nm.close()
+    return out
 
 
 def kernel_rev():
@@ -381,6 +427,9 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=2_000_000,
                     help="ratings per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target leg")
+    ap.add_argument("--ttt-scale", type=float, default=0.1,
+                    help="workload scale of the time-to-target leg")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
