@@ -36,11 +36,21 @@ constexpr int kRecBuf = 128;   // circular buffer of record positions
 constexpr int kRecInit = 64;   // positions loaded before the first row copy
 constexpr int kHeavy = 32;     // visits this long go first and are pushed at once
 
-constexpr int kRowChunks = 16;  // row-ring chunks per lane (16 bytes of binary32 each)
+constexpr int kStreamChunks = 16;  // row-ring chunks per lane of the generic stream
+constexpr int kBatchedWarps = 8;   // warps per thread block at most (register budget)
 
+constexpr int kVisitChunks = 21;   // ring chunks of a long visit at one chunk per lane
+
+// Row ring per lane: CHUNKS 16-byte chunks.  The generic stream uses the
+// first kStreamChunks and a long visit of the batch the first VISIT (each
+// runs alone); at one chunk per lane a visit of an urgent item that
+// interrupts either of them uses the kVisitChunks after those.
 template <int CPL>
 struct RowRing {
-  static constexpr int R = kRowChunks / CPL;  // slots; R-1 rows in flight
+  static constexpr int VISIT = CPL == 1 ? kVisitChunks : kStreamChunks;
+  static constexpr int CHUNKS = CPL == 1 ? 2 * kVisitChunks : kStreamChunks;
+  static constexpr int R = kStreamChunks / CPL;  // slots; R-1 rows in flight
+  static_assert(kStreamChunks <= VISIT, "the stream's slots lie in the batch's region");
 };
 
 // Storage of W and H: binary32 (a chunk of 4 entries is a float4) or
@@ -82,7 +92,7 @@ __device__ __forceinline__ uint2 pack_sr(float4 v, uint32_t ra, uint32_t rb) {
 // (int2) and two int4 tables of batch metadata.
 template <int CPL, bool BF>
 __host__ __device__ constexpr int warp_smem_bytes() {
-  return int((RowRing<CPL>::R + kBatch) * CPL * 32 * sizeof(typename Storage<BF>::chunk_t)) +
+  return int((RowRing<CPL>::CHUNKS + kBatch * CPL) * 32 * sizeof(typename Storage<BF>::chunk_t)) +
          kRecBuf * 8 + 2 * kBatch * 16;
 }
 
@@ -156,12 +166,12 @@ __device__ __forceinline__ float warp_sum_transposed(float (&v)[32], int lane) {
 // this is the sequential update; the dependent chain per rating shrinks from
 // a full warp reduction to one shuffle and one multiply-add.
 //
-// W rows come through the warp's shared-memory ring (`rows`, kRowChunks
-// chunk slots per lane), LB blocks ahead with cp.async; each lane copies and
-// reads only its own chunk of a row.  Records are held in lane registers,
+// W rows come through NCH chunk slots per lane of the warp's shared-memory
+// ring (`rows`), LB blocks ahead with cp.async; each lane copies and reads
+// only its own chunk of a row.  Records are held in lane registers,
 // three 32-record chunks (lane i holds record i of a chunk).  Earlier stores
 // of this warp precede these loads in program order.
-template <int CPL, bool BF, bool DEBUG>
+template <int CPL, bool BF, bool DEBUG, int NCH>
 __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF>::chunk_t* rows,
                                            typename Storage<BF>::chunk_t* W4, int64_t pitch4,
                                            int k4, const int2* __restrict__ rec, int64_t beg,
@@ -170,8 +180,9 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
   constexpr int B = CPL == 4 ? 4 : 7;
   constexpr int NS = B + B * (B - 1) / 2;
   static_assert(NS <= 32, "one transposed reduction per block");
-  constexpr int LB = (kRowChunks / CPL) / B;  // blocks of rows in flight
-  // positions up to B*(b + LB) + B - 1 lie in record chunks c0 and c0 + 1
+  // blocks of rows in flight; positions up to B*(b + LB) + B - 1 must lie in
+  // record chunks c0 and c0 + 1
+  constexpr int LB = (NCH / CPL) / B < 33 / B - 1 ? (NCH / CPL) / B : 33 / B - 1;
   static_assert(LB >= 1 && B * (LB + 1) - 1 <= 32, "row ring holds the blocks in flight");
   using chunk_t = typename Storage<BF>::chunk_t;
   const float al = 1.f - s * lam;
@@ -330,9 +341,76 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
   cp_wait<0>();
 }
 
+// A visit of an urgent item's token taken out of turn by worker q (one
+// 16-byte chunk of a row per lane): segment `useg`, just popped from q's
+// ring.  The steps of a long visit of a batch: metadata, h_j into registers,
+// the updates (in the ring slots `rows`, disjoint from those of the
+// interrupted work), h_j back to H, the token handed on at once.  Visits are
+// never split: the check runs between visits.  Not inlined: it is reached from
+// two places and runs a few hundred times per worker and epoch.
+template <bool BF, bool DEBUG>
+__device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, uint32_t useg,
+                                          typename Storage<BF>::chunk_t* rows) {
+  using chunk_t = typename Storage<BF>::chunk_t;
+  chunk_t* __restrict__ W4 = reinterpret_cast<chunk_t*>(P.W);
+  chunk_t* __restrict__ H4 = reinterpret_cast<chunk_t*>(P.H);
+  const int64_t pitch4 = P.pitch >> 2;
+  const int k4 = P.k4;
+  const uint2 seed = make_uint2(P.seed_lo, P.seed_hi);
+  const int uj = __ldg(P.seg_col + useg);
+  const int64_t ubeg = __ldg(P.seg_ptr + useg);
+  const int uc = int(__ldg(P.seg_ptr + useg + 1) - ubeg);
+  const int ue = __ldcg(P.tok_epoch + uj);
+  const int uhop = __ldcg(P.tok_hop + uj);
+  const int ucb = __ldg(P.col_seg_ptr + uj);
+  const int ud = __ldg(P.col_seg_ptr + uj + 1) - ucb;
+  float4 uh[1];
+  uh[0] = lane < k4 ? Storage<BF>::widen(__ldcg(H4 + int64_t(uj) * pitch4 + lane))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float us = __ldg(P.step + (ue - P.epoch0));
+  int unh = uhop + 1, une = ue;
+  if (unh == ud) {
+    unh = 0;
+    une = ue + 1;
+  }
+  int unseg = -1, uq2 = -1;
+  if (une < P.epoch0 + P.n_epochs) {
+    const uint4 key = philox4x32_10(
+        make_uint4(uint32_t(uj), uint32_t(une), 0u, kTagItinerary), seed);
+    unseg = __ldg(P.col_segs + ucb + itinerary_slot(uint32_t(unh), uint32_t(ud), key));
+    uq2 = __ldg(P.seg_worker + unseg);
+  }
+  if (DEBUG && lane == 0) {
+    const uint32_t tk = atomicAdd(P.log_ticket, 1u);
+    if (int64_t(tk) < P.log_cap) {
+      P.log_seg[tk] = int(useg);
+      P.log_epoch[tk] = ue;
+    }
+    if (atomicExch(P.owner + uj, q) != -1) flag_ownership(P, q, uj);
+  }
+  long_visit<1, BF, DEBUG, kVisitChunks>(uh, rows, W4, pitch4, k4, P.rec, ubeg, uc, us,
+                                         P.lambda, ue, seed, lane, P.rec_count);
+  if (lane < k4) {
+    if constexpr (BF) {
+      const uint4 rb = philox4x32_10(
+          make_uint4(useg, uint32_t(ue), 0u, 0x48000000u | uint32_t(lane)), seed);
+      __stcg(H4 + int64_t(uj) * pitch4 + lane, pack_sr(uh[0], rb.z, rb.w));
+    } else {
+      __stcg(H4 + int64_t(uj) * pitch4 + lane, uh[0]);
+    }
+  }
+  if (lane == 0) {
+    __stcg(P.tok_hop + uj, unh);
+    __stcg(P.tok_epoch + uj, une);
+    if (DEBUG && atomicExch(P.owner + uj, -1) != q) flag_ownership(P, q, uj);
+  }
+  __syncwarp();  // orders every lane's H stores before the release below
+  if (lane == 0 && unseg >= 0) push_urgent(P, uq2, uint32_t(unseg));
+}
+
 template <int CPL, bool BF, bool DEBUG>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32)
-nomad_batched_kernel(const SgdParams P) {
+__global__ void __launch_bounds__(kBatchedWarps * 32, 1)
+nomad_batched_kernel(const __grid_constant__ SgdParams P) {
   constexpr int R = RowRing<CPL>::R;
   using chunk_t = typename Storage<BF>::chunk_t;
   extern __shared__ float4 smem_f4[];
@@ -342,7 +420,7 @@ nomad_batched_kernel(const SgdParams P) {
   if (q >= P.p) return;
   chunk_t* rows = reinterpret_cast<chunk_t*>(reinterpret_cast<unsigned char*>(smem_f4) +
                                              size_t(wib) * warp_smem_bytes<CPL, BF>());
-  chunk_t* hbuf = rows + R * CPL * 32;
+  chunk_t* hbuf = rows + RowRing<CPL>::CHUNKS * 32;
   int2* recs = reinterpret_cast<int2*>(hbuf + kBatch * CPL * 32);
   int4* meta_a = reinterpret_cast<int4*>(recs + kRecBuf);  // {j, c, e, seg}
   int4* meta_b = meta_a + kBatch;                          // {beg_lo, beg_hi, lane, soff}
@@ -362,6 +440,47 @@ nomad_batched_kernel(const SgdParams P) {
 
   uint32_t head = 0;
   int64_t done = 0;
+  // urgent ring: tokens of the items with most ratings, taken out of turn
+  const bool use_u = CPL == 1 && P.use_urgent != 0;
+  const int lgu = P.uring_log2;
+  const uint32_t umask = (1u << lgu) - 1u;
+  const unsigned long long* uring_q = use_u ? P.uring + (int64_t(q) << lgu) : nullptr;
+  uint32_t head_u = 0;
+  // lane 0: urgent slot `pv_pos` as read at the previous check
+  unsigned long long pv = 0;
+  uint32_t pv_pos = ~0u;
+
+  // Between visits: take a token waiting in the urgent ring.  Lane 0 looks
+  // at the slot as read at the previous check (reading it again for the next
+  // check while it is empty), so the check never waits for memory.  Returns
+  // true after such a visit.
+  auto try_urgent = [&]() -> bool {
+    if constexpr (CPL != 1) {
+      return false;
+    } else {
+      if (!use_u) return false;
+      int go = 0;
+      uint32_t useg = 0;
+      if (lane == 0) {
+        if (pv_pos == head_u && uint32_t(pv >> 32) == (head_u >> lgu)) {
+          go = 1;
+          useg = uint32_t(pv);
+          fence_acq_rel_gpu();  // with the relaxed read of the slot: an acquire
+        } else {
+          pv = ld_relaxed_u64(uring_q + (head_u & umask));
+          pv_pos = head_u;
+        }
+      }
+      if (!__shfl_sync(kFull, go, 0)) return false;
+      __syncwarp();
+      useg = __shfl_sync(kFull, useg, 0);
+      ++head_u;
+      ++done;
+      urgent_visit<BF, DEBUG>(P, q, lane, useg, rows + kVisitChunks * 32);
+      return true;
+    }
+  };
+
   while (done < quota) {
     // ---- 1. the ready prefix of the ring
     const int want = quota - done < kBatch ? int(quota - done) : kBatch;
@@ -371,14 +490,25 @@ nomad_batched_kernel(const SgdParams P) {
       const uint32_t pos = head + uint32_t(lane);
       sv = ld_acquire_u64(ring_q + (pos & qmask));
       ready = uint32_t(sv >> 32) == (pos >> lg);
+    } else if (lane == 31 && use_u) {  // the urgent ring, read alongside
+      sv = ld_acquire_u64(uring_q + (head_u & umask));
+      ready = uint32_t(sv >> 32) == (head_u >> lgu);
     }
     const unsigned rmask = __ballot_sync(kFull, ready);
+    if (rmask >> 31) {  // an urgent item's token first
+      __syncwarp();
+      const uint32_t useg = uint32_t(__shfl_sync(kFull, sv, 31));
+      ++head_u;
+      ++done;
+      urgent_visit<BF, DEBUG>(P, q, lane, useg, rows + kVisitChunks * 32);
+      continue;
+    }
     const int nb = __ffs(~rmask) - 1;
     if (nb <= 0) {
       int got = 0;
-      if (lane == 0) got = pop_token(P, q, head, lg, ring_q);
+      if (lane == 0) got = wait_rings(P, q, head, lg, ring_q, head_u, uring_q);
       if (__shfl_sync(kFull, got, 0) < 0) return;
-      continue;  // the slot at head is ready now; take the prefix again
+      continue;  // a slot is ready now; read the rings again
     }
     __syncwarp();  // each lane's acquire precedes every lane's reads below
     head += uint32_t(nb);
@@ -477,6 +607,8 @@ nomad_batched_kernel(const SgdParams P) {
 
     // ---- 5h. the long visits
     for (int kh = 0; kh < nhv; ++kh) {
+      while (try_urgent()) {
+      }
       const int4 ma = meta_a[kh];
       const int4 mb = meta_b[kh];
       const int vl = mb.z;
@@ -495,8 +627,8 @@ nomad_batched_kernel(const SgdParams P) {
         }
         if (atomicExch(P.owner + ma.x, q) != -1) flag_ownership(P, q, ma.x);
       }
-      long_visit<CPL, BF, DEBUG>(hh, rows, W4, pitch4, k4, P.rec, vb, ma.y, sv, lam, ma.z, seed,
-                                 lane, P.rec_count);
+      long_visit<CPL, BF, DEBUG, RowRing<CPL>::VISIT>(hh, rows, W4, pitch4, k4, P.rec, vb, ma.y,
+                                                      sv, lam, ma.z, seed, lane, P.rec_count);
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
@@ -557,6 +689,11 @@ nomad_batched_kernel(const SgdParams P) {
     for (int cc = 0; cc < CPL; ++cc) h[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int t = T0; t < T; ++t) {
       if (t == vend) {  // a visit starts
+        // an urgent item's token waiting in the ring goes first: the tokens
+        // of the items with most ratings make the longest chains of visits
+        if (try_urgent()) {
+          if (lane < R) dflag = 1;  // the stream's rows copied before may be stale
+        }
         ++k;
         const int4 ma = meta_a[k];
         const int4 mb = meta_b[k];

@@ -313,6 +313,49 @@ __global__ void count_by(const int32_t* __restrict__ ids, int64_t n,
     atomicAdd(&counts[ids[s]], 1u);
 }
 
+// Ratings of each item, summed over its segments.
+__global__ void item_degrees(const int64_t* __restrict__ seg_ptr,
+                             const int32_t* __restrict__ seg_col, int64_t S,
+                             uint32_t* __restrict__ deg) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < S; s += stride)
+    atomicAdd(&deg[seg_col[s]], uint32_t(seg_ptr[s + 1] - seg_ptr[s]));
+}
+
+__global__ void max_u32(const uint32_t* __restrict__ x, int64_t n, uint32_t* __restrict__ out) {
+  uint32_t m = 0;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    m = x[i] > m ? x[i] : m;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Items whose tokens take the longest chains of visits: at least half the
+// ratings of the most-rated item.
+__global__ void urgent_flags(const uint32_t* __restrict__ deg, int64_t n,
+                             const uint32_t* __restrict__ max_deg, uint8_t* __restrict__ flag) {
+  const uint64_t top = *max_deg;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += stride)
+    flag[j] = deg[j] > 0 && 2ull * deg[j] >= top ? 1 : 0;
+}
+
+__global__ void count_flags(const uint8_t* __restrict__ flag, int64_t n,
+                            uint32_t* __restrict__ count) {
+  uint32_t c = 0;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += stride)
+    c += flag[j];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 __global__ void iota_u32(uint32_t* __restrict__ out, int64_t n) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += stride)
@@ -528,6 +571,33 @@ int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
   // 10. token state and debug arrays
   TRY(dev_alloc(h, &vp, sizeof(int32_t) * (n + 1))); h->tok_hop = (int32_t*)vp;
   TRY(dev_alloc(h, &vp, sizeof(int32_t) * (n + 1))); h->tok_epoch = (int32_t*)vp;
+  TRY(dev_alloc(h, &vp, sizeof(uint8_t) * (n + 1))); h->item_urgent = (uint8_t*)vp;
+  {
+    uint32_t* deg = nullptr;
+    TRY(cudaMallocAsync(&deg, sizeof(uint32_t) * (n + 2), st));
+    TRY(cudaMemsetAsync(deg, 0, sizeof(uint32_t) * (n + 2), st));
+    if (S > 0) {
+      item_degrees<<<grid_for(S), 256, 0, st>>>(h->seg_ptr, h->seg_col, S, deg);
+      ++t_launches;
+    }
+    if (n > 0) {
+      max_u32<<<grid_for(n), 256, 0, st>>>(deg, n, deg + n);
+      urgent_flags<<<grid_for(n), 256, 0, st>>>(deg, n, deg + n, h->item_urgent);
+      count_flags<<<grid_for(n), 256, 0, st>>>(h->item_urgent, n, deg + n + 1);
+      t_launches += 3;
+    }
+    uint32_t n_urgent = 0;
+    TRY(cudaMemcpyAsync(&n_urgent, deg + n + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    cudaFreeAsync(deg, st);
+    // one urgent ring per worker, room for every urgent token at once
+    int lgu = 5;
+    while ((int64_t(1) << lgu) < int64_t(n_urgent) + 1) ++lgu;
+    h->uring_log2 = lgu;
+    TRY(dev_alloc(h, &vp, sizeof(unsigned long long) * (int64_t(p) << lgu)));
+    h->uring = (unsigned long long*)vp;
+    TRY(dev_alloc(h, &vp, sizeof(uint32_t) * (p + 1))); h->uring_tail = (uint32_t*)vp;
+  }
   if (h->sched.debug || h->sched.mode == NOMAD_MODE_UNIFORM) {
     TRY(dev_alloc(h, &vp, sizeof(int32_t) * nalloc)); h->rec_count = (int32_t*)vp;
     TRY(cudaMemsetAsync(h->rec_count, 0, sizeof(int32_t) * nalloc, st));

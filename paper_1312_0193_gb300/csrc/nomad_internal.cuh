@@ -102,8 +102,13 @@ struct SgdParams {
   const int64_t* ring_base; // p
   const int32_t* ring_log2; // p: log2 of the ring capacity
   uint32_t* ring_tail;      // p: producer reservation counters
+  unsigned long long* uring;  // p x 2^uring_log2 slots: tokens of urgent items
+  uint32_t* uring_tail;       // p
+  int32_t uring_log2;
+  int32_t use_urgent;         // urgent items travel through the urgent rings
   int32_t* tok_hop;         // n: hop within the current epoch
   int32_t* tok_epoch;       // n: absolute epoch of the token
+  const uint8_t* item_urgent;  // n: 1 for the items with the most ratings
   const float* step;        // n_epochs step sizes (epoch mode)
   int32_t epoch0;
   int32_t n_epochs;
@@ -176,8 +181,12 @@ struct nomad_handle {
   int64_t* ring_base = nullptr;
   int32_t* ring_log2 = nullptr;
   uint32_t* ring_tail = nullptr;
+  unsigned long long* uring = nullptr;  // per worker: tokens of urgent items
+  uint32_t* uring_tail = nullptr;
+  int32_t uring_log2 = 0;
   int32_t* tok_hop = nullptr;
   int32_t* tok_epoch = nullptr;
+  uint8_t* item_urgent = nullptr;  // n: item degree >= half the largest
   float* step = nullptr;
   int32_t step_cap = 0;
   int32_t* status = nullptr;       // kStatusWords

@@ -139,7 +139,8 @@ __global__ void seed_tokens(const SgdParams P, int64_t n) {
           make_uint4(uint32_t(j), uint32_t(P.epoch0), 0u, kTagItinerary),
           make_uint2(P.seed_lo, P.seed_hi));
       const int seg = P.col_segs[base + itinerary_slot(0u, uint32_t(d), key)];
-      push_token(P, P.seg_worker[seg], uint32_t(seg));
+      if (P.use_urgent && P.item_urgent[j]) push_urgent(P, P.seg_worker[seg], uint32_t(seg));
+      else push_token(P, P.seg_worker[seg], uint32_t(seg));
     } else {
       const uint4 r = philox4x32_10(make_uint4(uint32_t(j), 0u, 0u, kTagUniform),
                                     make_uint2(P.seed_lo, P.seed_hi));
@@ -409,6 +410,13 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   P.ring_tail = h->ring_tail;
   P.tok_hop = h->tok_hop;
   P.tok_epoch = h->tok_epoch;
+  P.item_urgent = h->item_urgent;
+  P.uring = h->uring;
+  P.uring_tail = h->uring_tail;
+  P.uring_log2 = h->uring_log2;
+  // the batched kernel takes urgent items' visits out of turn (one chunk per lane)
+  P.use_urgent = (!uniform && h->sched.variant == NOMAD_VARIANT_BATCHED && h->k4 <= 32 &&
+                  h->uring != nullptr) ? 1 : 0;
   P.step = h->step;
   P.epoch0 = int32_t(h->epochs_done);
   P.n_epochs = n_epochs;
@@ -434,6 +442,10 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->ring, 0xff, sizeof(unsigned long long) * h->ring_slots, st)) ||
       (e = cudaMemsetAsync(h->ring_tail, 0, sizeof(uint32_t) * h->p, st)) ||
+      (h->uring && (e = cudaMemsetAsync(h->uring, 0xff,
+                                        sizeof(unsigned long long) * (int64_t(h->p) << h->uring_log2),
+                                        st))) ||
+      (h->uring_tail && (e = cudaMemsetAsync(h->uring_tail, 0, sizeof(uint32_t) * h->p, st))) ||
       (e = cudaMemsetAsync(h->status, 0, sizeof(int32_t) * kStatusWords, st))) {
     h->last_error = std::string("epoch: ") + cudaGetErrorString(e);
     return NOMAD_ERR_CUDA;

@@ -10,6 +10,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kDefaultWarpsPerBlock = 8;
 constexpr int kMaxWarpsPerBlock = 16;
+constexpr unsigned kMaxSleepNs = 512;  // longest back-off of a waiting worker
 
 __device__ __forceinline__ float warp_sum(float v) {
   v += __shfl_xor_sync(kFull, v, 16);
@@ -52,6 +53,50 @@ __device__ __forceinline__ void push_token(const SgdParams& P, int q,
   st_release_u64(slot, (static_cast<unsigned long long>(pos >> lg) << 32) | payload);
 }
 
+// Appends `payload` to worker q's urgent ring (the tokens of the items with
+// most ratings), with the same release store as push_token.
+__device__ __forceinline__ void push_urgent(const SgdParams& P, int q, uint32_t payload) {
+  const uint32_t pos = atomicAdd(P.uring_tail + q, 1u);
+  const int lg = P.uring_log2;
+  unsigned long long* slot = P.uring + (int64_t(q) << lg) + (pos & ((1u << lg) - 1u));
+  st_release_u64(slot, (static_cast<unsigned long long>(pos >> lg) << 32) | payload);
+}
+
+// Lane 0 only.  Waits until worker q's ring has a token at `head` or, when
+// `uring_q` is not null, its urgent ring one at `head_u`; 0 then, -1 when the
+// wait gave up (as pop_token).  The caller reads the slots again.
+__device__ int wait_rings(const SgdParams& P, int q, uint32_t head, int lg,
+                          const unsigned long long* ring_q, uint32_t head_u,
+                          const unsigned long long* uring_q) {
+  const unsigned long long* slot = ring_q + (head & ((1u << lg) - 1u));
+  const uint32_t lap = head >> lg;
+  const int lgu = P.uring_log2;
+  const unsigned long long* uslot = uring_q ? uring_q + (head_u & ((1u << lgu) - 1u)) : nullptr;
+  const uint32_t ulap = head_u >> lgu;
+  const unsigned long long t0 = globaltimer_ns();
+  const unsigned long long max_iters =
+      static_cast<unsigned long long>(P.timeout_ns) / 16ull + (1ull << 20);
+  unsigned ns = 32;
+  for (unsigned long long it = 0; it < max_iters; ++it) {
+    if (uint32_t(ld_relaxed_u64(slot) >> 32) == lap ||
+        (uslot && uint32_t(ld_relaxed_u64(uslot) >> 32) == ulap)) {
+      fence_acq_rel_gpu();
+      return 0;
+    }
+    if ((it & 15) == 15) {
+      if (ld_relaxed_i32(P.status) != 0) return -1;
+      if (globaltimer_ns() - t0 > static_cast<unsigned long long>(P.timeout_ns)) break;
+    }
+    __nanosleep(ns);
+    if (ns < kMaxSleepNs) ns <<= 1;
+  }
+  if (atomicCAS(P.status, 0, NOMAD_ERR_TIMEOUT) == 0) {
+    atomicExch(P.status + 1, q);
+    atomicExch(P.status + 2, int(head));
+  }
+  return -1;
+}
+
 // Lane 0 only.  Returns the payload at position `head` of worker q's ring,
 // or -1 when the wait gave up (another worker failed, the stop flag of
 // uniform mode was raised, or this wait exceeded the timeout, in which case
@@ -59,7 +104,6 @@ __device__ __forceinline__ void push_token(const SgdParams& P, int q,
 // acquire load would also invalidate the SM's L1, which the working warps of
 // the SM use) and a backoff of up to kMaxSleepNs; the acquire is one fence
 // once the slot is seen ready.
-constexpr unsigned kMaxSleepNs = 512;
 __device__ int pop_token(const SgdParams& P, int q, uint32_t head, int lg,
                          const unsigned long long* ring_q) {
   const unsigned long long* slot = ring_q + (head & ((1u << lg) - 1u));

@@ -181,11 +181,12 @@ def test_replay_tiny_large_steps(tiny, variant):
     replay_check(tiny, 10, 0.05, 0.1, 0.01, 20, p=64, variant=variant)
 
 
-@pytest.mark.parametrize("p", [4, 16])
+@pytest.mark.parametrize("p", [4, 16, 64])
 def test_replay_few_workers_long_visits(p):
     """Few workers: long visits (>= 32 ratings, pushed right after their
-    visit), many rows shared between the visits of one batch (the
-    prefetch-hazard path), records streamed in several chunks."""
+    visit, and taken out of turn when they arrive during another batch's
+    stream of short visits), many rows shared between the visits of one
+    batch (the prefetch-hazard path), records streamed in several chunks."""
     r = synth.netflix_shaped(0.002, seed=13)
     replay_check(r, 100, 0.05, 0.01, 0.05, 2, p=p)
 
