@@ -349,7 +349,7 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
 // never split: the check runs between visits.  Not inlined: it is reached from
 // two places and runs a few hundred times per worker and epoch.
 template <bool BF, bool DEBUG>
-__device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, uint32_t useg,
+__device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, uint32_t item,
                                           typename Storage<BF>::chunk_t* rows) {
   using chunk_t = typename Storage<BF>::chunk_t;
   chunk_t* __restrict__ W4 = reinterpret_cast<chunk_t*>(P.W);
@@ -357,13 +357,16 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
   const int64_t pitch4 = P.pitch >> 2;
   const int k4 = P.k4;
   const uint2 seed = make_uint2(P.seed_lo, P.seed_hi);
-  const int uj = __ldg(P.seg_col + useg);
-  const int64_t ubeg = __ldg(P.seg_ptr + useg);
-  const int uc = int(__ldg(P.seg_ptr + useg + 1) - ubeg);
-  const int ue = __ldcg(P.tok_epoch + uj);
-  const int uhop = __ldcg(P.tok_hop + uj);
-  const int ucb = __ldg(P.col_seg_ptr + uj);
-  const int ud = __ldg(P.col_seg_ptr + uj + 1) - ucb;
+  const int uj = int(item);
+  const int4 ra = __ldcg(P.tok_rec + 2 * uj);
+  const int4 rb4 = __ldcg(P.tok_rec + 2 * uj + 1);
+  const uint32_t useg = uint32_t(ra.x);
+  const int uc = ra.y;
+  const int64_t ubeg = int64_t(uint32_t(ra.z));
+  const int ue = ra.w;
+  const int uhop = rb4.x;
+  const int ucb = rb4.y;
+  const int ud = rb4.z;
   float4 uh[1];
   uh[0] = lane < k4 ? Storage<BF>::widen(__ldcg(H4 + int64_t(uj) * pitch4 + lane))
                     : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -373,12 +376,15 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
     unh = 0;
     une = ue + 1;
   }
-  int unseg = -1, uq2 = -1;
+  int unseg = -1, uq2 = -1, unc = 0;
+  int64_t unbeg = 0;
   if (une < P.epoch0 + P.n_epochs) {
     const uint4 key = philox4x32_10(
         make_uint4(uint32_t(uj), uint32_t(une), 0u, kTagItinerary), seed);
     unseg = __ldg(P.col_segs + ucb + itinerary_slot(uint32_t(unh), uint32_t(ud), key));
     uq2 = __ldg(P.seg_worker + unseg);
+    unbeg = __ldg(P.seg_ptr + unseg);
+    unc = int(__ldg(P.seg_ptr + unseg + 1) - unbeg);
   }
   if (DEBUG && lane == 0) {
     const uint32_t tk = atomicAdd(P.log_ticket, 1u);
@@ -400,12 +406,14 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
     }
   }
   if (lane == 0) {
-    __stcg(P.tok_hop + uj, unh);
-    __stcg(P.tok_epoch + uj, une);
+    if (unseg >= 0) {
+      __stcg(P.tok_rec + 2 * uj, make_int4(unseg, unc, int(uint32_t(unbeg)), une));
+      __stcg(P.tok_rec + 2 * uj + 1, make_int4(unh, ucb, ud, 0));
+    }
     if (DEBUG && atomicExch(P.owner + uj, -1) != q) flag_ownership(P, q, uj);
   }
   __syncwarp();  // orders every lane's H stores before the release below
-  if (lane == 0 && unseg >= 0) push_urgent(P, uq2, uint32_t(unseg));
+  if (lane == 0 && unseg >= 0) push_urgent(P, uq2, uint32_t(uj));
 }
 
 template <int CPL, bool BF, bool DEBUG>
@@ -514,22 +522,21 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     head += uint32_t(nb);
     done += nb;
     const bool mine = lane < nb;
-    const int seg = mine ? int(uint32_t(sv)) : 0;
 
-    // ---- 2. metadata of token `lane`
-    int j = 0, c = 0;
+    // ---- 2. token `lane`: item from the ring, its visit from its record
+    int j = 0, seg = 0, c = 0, e = 0, hop = 0, cb = 0, dseg = 0;
     int64_t beg = 0;
     if (mine) {
-      j = __ldg(P.seg_col + seg);
-      beg = __ldg(P.seg_ptr + seg);
-      c = int(__ldg(P.seg_ptr + seg + 1) - beg);
-    }
-    int e = 0, hop = 0, cb = 0, cend = 0;
-    if (mine) {
-      e = __ldcg(P.tok_epoch + j);
-      hop = __ldcg(P.tok_hop + j);
-      cb = __ldg(P.col_seg_ptr + j);
-      cend = __ldg(P.col_seg_ptr + j + 1);
+      j = int(uint32_t(sv));
+      const int4 ra = __ldcg(P.tok_rec + 2 * j);
+      const int4 rb4 = __ldcg(P.tok_rec + 2 * j + 1);
+      seg = ra.x;
+      c = ra.y;
+      beg = int64_t(uint32_t(ra.z));
+      e = ra.w;
+      hop = rb4.x;
+      cb = rb4.y;
+      dseg = rb4.z;
     }
 
     // ---- 3. processing order: long visits first, then ring order
@@ -584,7 +591,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     float s_tok = 0.f;
     if (mine) {
       s_tok = __ldg(P.step + (e - P.epoch0));
-      const int d = cend - cb;
+      const int d = dseg;
       nh = hop + 1;
       ne = e;
       if (nh == d) {
@@ -602,8 +609,20 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     }
     cp_wait_all();
     __syncwarp();
-    int q2 = -1;
-    if (mine && nseg >= 0) q2 = __ldg(P.seg_worker + nseg);
+    int q2 = -1, nc = 0;  // the next visit: worker, length, first record
+    int64_t nbeg = 0;
+    if (mine && nseg >= 0) {
+      q2 = __ldg(P.seg_worker + nseg);
+      nbeg = __ldg(P.seg_ptr + nseg);
+      nc = int(__ldg(P.seg_ptr + nseg + 1) - nbeg);
+    }
+    // the token's record for its next visit, written before its release
+    auto write_record = [&]() {
+      if (nseg >= 0) {
+        __stcg(P.tok_rec + 2 * j, make_int4(nseg, nc, int(uint32_t(nbeg)), ne));
+        __stcg(P.tok_rec + 2 * j + 1, make_int4(nh, cb, dseg, 0));
+      }
+    };
 
     // ---- 5h. the long visits
     for (int kh = 0; kh < nhv; ++kh) {
@@ -643,12 +662,11 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
         }
       }
       if (lane == vl) {
-        __stcg(P.tok_hop + j, nh);
-        __stcg(P.tok_epoch + j, ne);
+        write_record();
         if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
       }
       __syncwarp();  // orders every lane's H stores before the release below
-      if (lane == vl && nseg >= 0) push_token(P, q2, uint32_t(nseg));
+      if (lane == vl && nseg >= 0) push_token(P, q2, uint32_t(j));
     }
 
     // ---- 5a. cold start of the row ring: positions 0 .. R-2
@@ -804,12 +822,11 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     // ---- 6. hand on the remaining tokens together
     const bool late = mine && c < kHeavy;
     if (late) {
-      __stcg(P.tok_hop + j, nh);
-      __stcg(P.tok_epoch + j, ne);
+      write_record();
       if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
     }
     __syncwarp();  // orders every lane's H stores before the releases below
-    if (late && nseg >= 0) push_token(P, q2, uint32_t(nseg));
+    if (late && nseg >= 0) push_token(P, q2, uint32_t(j));
   }
 }
 

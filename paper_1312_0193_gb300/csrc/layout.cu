@@ -572,6 +572,7 @@ int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
   TRY(dev_alloc(h, &vp, sizeof(int32_t) * (n + 1))); h->tok_hop = (int32_t*)vp;
   TRY(dev_alloc(h, &vp, sizeof(int32_t) * (n + 1))); h->tok_epoch = (int32_t*)vp;
   TRY(dev_alloc(h, &vp, sizeof(uint8_t) * (n + 1))); h->item_urgent = (uint8_t*)vp;
+  TRY(dev_alloc(h, &vp, sizeof(int4) * 2 * (n + 1))); h->tok_rec = (int4*)vp;
   {
     uint32_t* deg = nullptr;
     TRY(cudaMallocAsync(&deg, sizeof(uint32_t) * (n + 2), st));

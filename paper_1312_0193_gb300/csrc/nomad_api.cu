@@ -53,7 +53,8 @@ void free_layout(nomad_handle* h) {
                    (void**)&h->ring_base,  (void**)&h->ring_log2, (void**)&h->ring_tail,
                    (void**)&h->tok_hop,    (void**)&h->tok_epoch, (void**)&h->owner,
                    (void**)&h->rec_count,  (void**)&h->log_seg,   (void**)&h->log_epoch,
-                   (void**)&h->item_urgent, (void**)&h->uring,    (void**)&h->uring_tail};
+                   (void**)&h->item_urgent, (void**)&h->uring,    (void**)&h->uring_tail,
+                   (void**)&h->tok_rec};
   for (void** p : ptrs) dev_free(h, p);
   h->log_cap = 0;
   h->loaded = false;

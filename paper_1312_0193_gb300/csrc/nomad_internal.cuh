@@ -109,6 +109,10 @@ struct SgdParams {
   int32_t* tok_hop;         // n: hop within the current epoch
   int32_t* tok_epoch;       // n: absolute epoch of the token
   const uint8_t* item_urgent;  // n: 1 for the items with the most ratings
+  // batched kernel: per item, the token's next visit {segment, length, first
+  // record, epoch} and {hop, first of its segments, number of segments, 0};
+  // ring payloads are then item ids (null: payloads are segment ids)
+  int4* tok_rec;
   const float* step;        // n_epochs step sizes (epoch mode)
   int32_t epoch0;
   int32_t n_epochs;
@@ -187,6 +191,7 @@ struct nomad_handle {
   int32_t* tok_hop = nullptr;
   int32_t* tok_epoch = nullptr;
   uint8_t* item_urgent = nullptr;  // n: item degree >= half the largest
+  int4* tok_rec = nullptr;         // 2n: next-visit record of each token
   float* step = nullptr;
   int32_t step_cap = 0;
   int32_t* status = nullptr;       // kStatusWords

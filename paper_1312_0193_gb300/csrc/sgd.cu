@@ -139,8 +139,16 @@ __global__ void seed_tokens(const SgdParams P, int64_t n) {
           make_uint4(uint32_t(j), uint32_t(P.epoch0), 0u, kTagItinerary),
           make_uint2(P.seed_lo, P.seed_hi));
       const int seg = P.col_segs[base + itinerary_slot(0u, uint32_t(d), key)];
-      if (P.use_urgent && P.item_urgent[j]) push_urgent(P, P.seg_worker[seg], uint32_t(seg));
-      else push_token(P, P.seg_worker[seg], uint32_t(seg));
+      if (P.tok_rec) {  // the batched kernel: the next-visit record, item payloads
+        const int64_t b0 = P.seg_ptr[seg];
+        P.tok_rec[2 * j] = make_int4(seg, int(P.seg_ptr[seg + 1] - b0), int(uint32_t(b0)),
+                                     P.epoch0);
+        P.tok_rec[2 * j + 1] = make_int4(0, base, d, 0);
+        if (P.use_urgent && P.item_urgent[j]) push_urgent(P, P.seg_worker[seg], uint32_t(j));
+        else push_token(P, P.seg_worker[seg], uint32_t(j));
+      } else {
+        push_token(P, P.seg_worker[seg], uint32_t(seg));
+      }
     } else {
       const uint4 r = philox4x32_10(make_uint4(uint32_t(j), 0u, 0u, kTagUniform),
                                     make_uint2(P.seed_lo, P.seed_hi));
@@ -411,6 +419,7 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   P.tok_hop = h->tok_hop;
   P.tok_epoch = h->tok_epoch;
   P.item_urgent = h->item_urgent;
+  P.tok_rec = (!uniform && h->sched.variant == NOMAD_VARIANT_BATCHED) ? h->tok_rec : nullptr;
   P.uring = h->uring;
   P.uring_tail = h->uring_tail;
   P.uring_log2 = h->uring_log2;
