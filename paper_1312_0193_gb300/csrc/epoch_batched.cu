@@ -446,7 +446,8 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
   const int epoch_end = P.epoch0 + P.n_epochs;
   const unsigned below = (1u << lane) - 1u;
 
-  uint32_t head = 0;
+  uint32_t head = 0;      // first ring position not yet taken
+  uint32_t taken = 0;     // bit i: position head + i already taken (out of order)
   int64_t done = 0;
   // urgent ring: tokens of the items with most ratings, taken out of turn
   const bool use_u = CPL == 1 && P.use_urgent != 0;
@@ -490,14 +491,17 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
   };
 
   while (done < quota) {
-    // ---- 1. the ready prefix of the ring
-    const int want = quota - done < kBatch ? int(quota - done) : kBatch;
+    // ---- 1. ready tokens among the first kRingWindow positions of the ring
+    // (a position reserved by a pusher that has not written it yet does not
+    // hold back the ones behind it), and the urgent ring
     unsigned long long sv = 0;
     bool ready = false;
-    if (lane < want) {
+    if (lane < kRingWindow) {
       const uint32_t pos = head + uint32_t(lane);
-      sv = ld_acquire_u64(ring_q + (pos & qmask));
-      ready = uint32_t(sv >> 32) == (pos >> lg);
+      if (!((taken >> lane) & 1u)) {
+        sv = ld_acquire_u64(ring_q + (pos & qmask));
+        ready = uint32_t(sv >> 32) == (pos >> lg);
+      }
     } else if (lane == 31 && use_u) {  // the urgent ring, read alongside
       sv = ld_acquire_u64(uring_q + (head_u & umask));
       ready = uint32_t(sv >> 32) == (head_u >> lgu);
@@ -505,21 +509,33 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     const unsigned rmask = __ballot_sync(kFull, ready);
     if (rmask >> 31) {  // an urgent item's token first
       __syncwarp();
-      const uint32_t useg = uint32_t(__shfl_sync(kFull, sv, 31));
+      const uint32_t item = uint32_t(__shfl_sync(kFull, sv, 31));
       ++head_u;
       ++done;
-      urgent_visit<BF, DEBUG>(P, q, lane, useg, rows + kVisitChunks * 32);
+      urgent_visit<BF, DEBUG>(P, q, lane, item, rows + kVisitChunks * 32);
       continue;
     }
-    const int nb = __ffs(~rmask) - 1;
-    if (nb <= 0) {
+    unsigned tmask = rmask & ((1u << kRingWindow) - 1u);
+    if (tmask == 0u) {
       int got = 0;
       if (lane == 0) got = wait_rings(P, q, head, lg, ring_q, head_u, uring_q);
       if (__shfl_sync(kFull, got, 0) < 0) return;
       continue;  // a slot is ready now; read the rings again
     }
+    // the first kBatch ready positions; batch lane b takes the b-th of them
+    while (__popc(tmask) > kBatch) tmask &= ~(1u << (31 - __clz(tmask)));
+    const int nb = __popc(tmask);
+    {
+      const int src = lane < nb ? int(__fns(tmask, 0, lane + 1)) : 0;
+      sv = __shfl_sync(kFull, sv, src);
+    }
     __syncwarp();  // each lane's acquire precedes every lane's reads below
-    head += uint32_t(nb);
+    taken |= tmask;
+    {
+      const int adv = __ffs(~taken) - 1;  // taken positions at the head
+      head += uint32_t(adv);
+      taken >>= adv;
+    }
     done += nb;
     const bool mine = lane < nb;
 
@@ -670,25 +686,36 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     }
 
     // ---- 5a. cold start of the row ring: positions 0 .. R-2
-    int win = -1;  // lane L < R: row of the latest position p with p % R == L
-    int dflag = 0; // lane L < R: that position is loaded directly (hazard)
+    // A row that a position in flight also updates (a user who rated two
+    // items of the batch) is not copied: the latest such position writes its
+    // updated row into this position's slot as well (each lane its own chunk).
+    int win = -1;    // lane L < R: row of the position in flight in slot L
+    int fwd = -1;    // lane L < R: the slot that takes that position's updated row
+    auto copy_row = [&](int slot, int row) {
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int idx = lane + 32 * cc;
+        if (idx < k4) {
+          if constexpr (BF) cp_async8(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
+          else cp_async16(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
+        }
+      }
+    };
     auto prefetch = [&](int pp) {
       const int slot = pp % R;
       const int row = recs[pp % kRecBuf].x;
-      const bool hz = __ballot_sync(kFull, lane < R && lane != slot && win == row) != 0u;
-      if (!hz) {
-#pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) {
-          const int idx = lane + 32 * cc;
-          if (idx < k4) {
-            if constexpr (BF) cp_async8(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
-            else cp_async16(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
-          }
-        }
+      const unsigned m = __ballot_sync(kFull, lane < R && lane != slot && win == row);
+      if (m) {
+        // the latest of those positions: going back from pp - 1 the slots are
+        // slot - 1, ..., 0, R - 1, ..., slot + 1
+        const unsigned mm = (m | (m << R)) & ((1u << (slot + R)) - 1u);
+        if (lane == (31 - __clz(mm)) % R) fwd = slot;
+      } else {
+        copy_row(slot, row);
       }
       if (lane == slot) {
         win = row;
-        dflag = hz ? 1 : 0;
+        fwd = -1;
       }
     };
     // one commit group per position: at tick t exactly R-1 groups are
@@ -710,7 +737,12 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
         // an urgent item's token waiting in the ring goes first: the tokens
         // of the items with most ratings make the longest chains of visits
         if (try_urgent()) {
-          if (lane < R) dflag = 1;  // the stream's rows copied before may be stale
+          // rows copied or forwarded for the positions in flight may be stale:
+          // copy them all again (a forward still to come overwrites the copy)
+          for (int pos = t; pos < t + R - 1 && pos < T; ++pos)
+            copy_row(pos % R, recs[pos % kRecBuf].x);
+          cp_commit();
+          cp_wait<0>();
         }
         ++k;
         const int4 ma = meta_a[k];
@@ -745,7 +777,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
         prefetch(pp);
       } else if (lane == pp % R) {
         win = -1;
-        dflag = 0;
+        fwd = -1;
       }
       cp_commit();
       cp_wait<R - 1>();
@@ -753,15 +785,14 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
 
       const int2 rc = recs[t % kRecBuf];
       const int slot = t % R;
-      const int direct = __shfl_sync(kFull, dflag, slot);
+      const int fslot = __shfl_sync(kFull, fwd, slot);  // a later position's slot, or -1
       chunk_t* wrow = W4 + int64_t(rc.x) * pitch4;
       float4 w[CPL];
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
         w[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < k4)
-          w[cc] = Storage<BF>::widen(direct ? __ldcg(wrow + idx) : rows[(slot * CPL + cc) * 32 + lane]);
+        if (idx < k4) w[cc] = Storage<BF>::widen(rows[(slot * CPL + cc) * 32 + lane]);
       }
       float part = 0.f;
 #pragma unroll
@@ -785,16 +816,19 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
         hn.z = fmaf(s, fmaf(err, w[cc].z, -lam * h[cc].z), h[cc].z);
         hn.w = fmaf(s, fmaf(err, w[cc].w, -lam * h[cc].w), h[cc].w);
         if (idx < k4) {
+          chunk_t out;
           if constexpr (BF) {
             const int64_t rix = vbeg + (t - vsoff);
             const uint4 rb = philox4x32_10(
                 make_uint4(uint32_t(rix), uint32_t(uint64_t(rix) >> 32), uint32_t(meta_a[k].z),
                            0x57000000u | uint32_t(idx)),
                 seed);
-            wrow[idx] = pack_sr(wn, rb.x, rb.y);
+            out = pack_sr(wn, rb.x, rb.y);
           } else {
-            wrow[idx] = wn;
+            out = wn;
           }
+          wrow[idx] = out;
+          if (fslot >= 0) rows[(fslot * CPL + cc) * 32 + lane] = out;
           h[cc] = hn;
         }
       }

@@ -376,7 +376,8 @@ __global__ void ring_sizes(const uint32_t* __restrict__ nseg, int32_t p,
                            int64_t* __restrict__ cap) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= p) return;
-  const int64_t need = uniform_items > 0 ? uniform_items : int64_t(nseg[q]);
+  const int64_t need =
+      (uniform_items > 0 ? uniform_items : int64_t(nseg[q])) + kRingWindow + 1;
   int lg = 5;  // at least 32 slots
   while ((int64_t(1) << lg) < need) ++lg;
   log2cap[q] = lg;

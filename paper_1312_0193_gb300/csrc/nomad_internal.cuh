@@ -48,6 +48,12 @@ constexpr uint32_t kTagItinerary = 0x49544e52u;  // epoch-mode visit orders
 constexpr uint32_t kTagUniform = 0x554e4946u;    // uniform-mode routing
 constexpr uint32_t kTagRounding = 0x53524e44u;   // stochastic rounding
 
+// A worker of the batched kernel takes ready tokens from the first
+// kRingWindow positions at the head of its ring, not only a contiguous
+// prefix; rings have kRingWindow slots of headroom for the positions taken
+// ahead of the head.
+constexpr int kRingWindow = 16;
+
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ unsigned long long ld_acquire_u64(
     const unsigned long long* p) {
