@@ -701,9 +701,8 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
         }
       }
     };
-    auto prefetch = [&](int pp) {
+    auto prefetch = [&](int pp, int row) {
       const int slot = pp % R;
-      const int row = recs[pp % kRecBuf].x;
       const unsigned m = __ballot_sync(kFull, lane < R && lane != slot && win == row);
       if (m) {
         // the latest of those positions: going back from pp - 1 the slots are
@@ -721,7 +720,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     // one commit group per position: at tick t exactly R-1 groups are
     // younger than position t's group, so cp.async.wait_group R-1 suffices
     for (int pp = T0; pp < T0 + R - 1; ++pp) {
-      if (pp < T) prefetch(pp);
+      if (pp < T) prefetch(pp, recs[pp % kRecBuf].x);
       cp_commit();
     }
 
@@ -732,6 +731,9 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     float4 h[CPL];
 #pragma unroll
     for (int cc = 0; cc < CPL; ++cc) h[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the row the next tick prefetches, read a tick ahead (its record landed
+    // with a group at least R ticks old)
+    int nrow = T0 + R - 1 < T ? recs[(T0 + R - 1) % kRecBuf].x : 0;
     for (int t = T0; t < T; ++t) {
       if (t == vend) {  // a visit starts
         // an urgent item's token waiting in the ring goes first: the tokens
@@ -774,7 +776,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
       }
       const int pp = t + R - 1;
       if (pp < T) {
-        prefetch(pp);
+        prefetch(pp, nrow);
       } else if (lane == pp % R) {
         win = -1;
         fwd = -1;
@@ -833,6 +835,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
         }
       }
       if (DEBUG && lane == 0) P.rec_count[vbeg + (t - vsoff)] += 1;
+      if (t + R < T) nrow = recs[(t + R) % kRecBuf].x;
 
       if (t == vend - 1) {  // the visit ends: publish h_j
         const int jv = meta_a[k].x;
