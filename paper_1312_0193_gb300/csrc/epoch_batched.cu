@@ -112,21 +112,20 @@ __device__ __forceinline__ void cp_wait() {
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Copies the records of stream positions [p0, p0 + count) (count <= 32) into
-// the circular buffer.  meta_a[r].y is the length and meta_b[r] = {beg_lo,
-// beg_hi, token lane, stream offset} of the rank-r visit.
-__device__ __forceinline__ void load_records(int2* recs, const int2* __restrict__ rec,
-                                             const int4* meta_a, const int4* meta_b, int nb,
-                                             int p0, int count, int lane) {
+// the circular buffer.  Lane r < nb holds the stream offset `soff` and first
+// record `beg` of the rank-r visit (offsets increase with the rank).
+__device__ __forceinline__ void load_records(int2* recs, const int2* __restrict__ rec, int soff,
+                                             int64_t beg, int nb, int p0, int count, int lane) {
   const int p = p0 + lane;
-  if (lane < count) {
-    int64_t src = 0;
-    for (int r = 0; r < nb; ++r) {
-      const int off = meta_b[r].w;
-      if (p >= off && p < off + meta_a[r].y)
-        src = ((int64_t(meta_b[r].y) << 32) | uint32_t(meta_b[r].x)) + (p - off);
-    }
-    cp_async8(recs + (p % kRecBuf), rec + src);
+  int r = 0;  // the visit of position p: the last rank whose offset is <= p
+#pragma unroll
+  for (int i = 1; i < kBatch; ++i) {
+    const int o = __shfl_sync(kFull, soff, i);
+    if (i < nb && o <= p) r = i;
   }
+  const int o = __shfl_sync(kFull, soff, r);
+  const int64_t b = __shfl_sync(kFull, beg, r);
+  if (lane < count) cp_async8(recs + (p % kRecBuf), rec + b + (p - o));
 }
 
 
@@ -591,6 +590,13 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
         }
       }
     }
+    int v_soff = 0;  // lane r < nb: stream offset and first record of the rank-r visit
+    int64_t v_beg = 0;
+    if (lane < nb) {
+      const int4 mb = meta_b[lane];
+      v_soff = mb.w;
+      v_beg = (int64_t(mb.y) << 32) | uint32_t(mb.x);
+    }
     // long visits (ranks 0 .. nhv-1) take stream positions [0, T0) and run
     // first on their own path; the generic stream starts at T0
     const int nhv = __popc(hv);
@@ -598,7 +604,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     for (int r = 0; r < nhv; ++r) T0 += meta_a[r].y;
     int loaded = T - T0 < kRecInit ? T : T0 + kRecInit;
     for (int p0 = T0; p0 < loaded; p0 += 32)
-      load_records(recs, P.rec, meta_a, meta_b, nb, p0, loaded - p0 < 32 ? loaded - p0 : 32,
+      load_records(recs, P.rec, v_soff, v_beg, nb, p0, loaded - p0 < 32 ? loaded - p0 : 32,
                    lane);
     cp_commit();
 
@@ -771,7 +777,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
       // keep the records one chunk ahead of the row prefetch
       if (loaded < T && loaded < t + R + 32) {
         const int cnt = T - loaded < 32 ? T - loaded : 32;
-        load_records(recs, P.rec, meta_a, meta_b, nb, loaded, cnt, lane);
+        load_records(recs, P.rec, v_soff, v_beg, nb, loaded, cnt, lane);
         loaded += cnt;
       }
       const int pp = t + R - 1;
