@@ -253,7 +253,7 @@ def run_ours(args):
     e2e_t, e2e_units = reduce_max_sum(e2e_local, float(nnz) * e2e_steps, world, dev)
     h2d = 12 * nnz + 12 * int(te_r.numel())
 
-    bytes_per_update = 2 * k * 4 + 8
+    bytes_per_update = 2 * k * (2 if args.precision == "bf16" else 4) + 8
     kern_avg_s = statistics.mean(kernel_ms) / 1000.0
     achieved_gbs = nnz * bytes_per_update / kern_avg_s / 1e9
     peak, peak_src = load_peaks()
