@@ -199,7 +199,7 @@ def run_ours(args):
     nnz = r.nnz
     nm = Nomad(r.m, r.n, k, lam, alpha=alpha, beta=beta, device=local,
                n_workers=args.workers, warps_per_block=args.warps_per_block,
-               precision=args.precision)
+               precision=args.precision, mode=args.mode, routing=args.routing)
     stream = torch.cuda.current_stream(dev)
     t_load0 = time.perf_counter()
     nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
@@ -290,7 +290,9 @@ def run_ours(args):
             "data": "synthetic (seeded; stands in for the paper's dataset)",
             "config": {
                 "workload": workload_name(r, k), "lambda": lam, "alpha": alpha,
-                "beta": beta, "mode": "epoch (permutation circulation)",
+                "beta": beta,
+                "mode": "epoch (permutation circulation)" if args.mode == "epoch" else
+                        "uniform (Alg. 1), %s routing" % args.routing,
                 "workers": info["p"], "warps_per_block": info["warps_per_block"],
                 "segments": info["n_segments"],
                 "ratings_per_visit": round(nnz / max(info["n_segments"], 1), 3),
@@ -304,7 +306,8 @@ def run_ours(args):
                          "unit": "GB/s", "frac": achieved_gbs / peak, "traffic": traffic,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
                          if peak_src == "measured" else "fallback 6.8 TB/s",
-                         "kernel": "nomad_batched_kernel", "kernel_ms": kern_avg_s * 1e3,
+                         "kernel": "nomad_batched_kernel" if args.mode == "epoch" else
+                                   "nomad_uniform_kernel", "kernel_ms": kern_avg_s * 1e3,
                          "bytes_per_update": bytes_per_update},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_units / e2e_t, "unit": UNIT,
@@ -417,6 +420,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="netflix")
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--mode", choices=["epoch", "uniform"], default="epoch",
+                    help="routing of tokens: permutation circulation or Alg. 1")
+    ap.add_argument("--routing", choices=["uniform", "shorter"], default="uniform",
+                    help="uniform mode: next worker uniform or the shorter of two queues")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (same shape) for profiler captures")
     ap.add_argument("--workers", type=int, default=0)

@@ -78,6 +78,12 @@ extern "C" {
                                    (default) */
 #define NOMAD_VARIANT_SIMPLE 1  /* a worker handles one token at a time */
 
+/* Uniform mode: choice of the next worker (Alg. 1 / Sec. 3.3). */
+#define NOMAD_ROUTING_UNIFORM 0  /* uniform over all p workers (Alg. 1) */
+#define NOMAD_ROUTING_SHORTER 1  /* of two workers drawn uniformly, the one with
+                                    fewer tokens waiting in its queue (dynamic
+                                    load balancing, Sec. 3.3) */
+
 #define NOMAD_COO 0 /* rating input as (row, col, value) triples */
 #define NOMAD_CSC 1 /* rating input as column pointers + row indices */
 
@@ -102,7 +108,7 @@ typedef struct nomad_schedule {
                        handed to a worker in nomad_epoch (a planted lost
                        message); -1 = none */
   int32_t variant;  /* epoch-mode worker kernel: NOMAD_VARIANT_* */
-  int32_t pad0;
+  int32_t routing;  /* uniform mode: NOMAD_ROUTING_* */
   int64_t reserved[5];
 } nomad_schedule;
 

@@ -54,7 +54,7 @@ def _lib():
         lib.orc_replay_f32.restype = i32
         lib.orc_serial_nomad.argtypes = [i32, f64, f64, f64, i32, i64, i64, P,
                                          P, P, P, P, P, P, i32, u64, i32, P, P,
-                                         P, P, i64]
+                                         P, P, i64, P]
         lib.orc_serial_nomad.restype = i64
         lib.orc_shuffled_sgd.argtypes = [i32, f64, f64, f64, i64, P, P, P, i32,
                                          u64, P, P, P]
@@ -259,9 +259,12 @@ def replay(layout: dict, visit_seg, W, H, lam: float, alpha: float,
 
 def serial_nomad(layout: dict, W, H, lam: float, alpha: float, beta: float,
                  n_epochs: int, seed: int, mode: str = "epoch",
-                 log_cap: int = 0):
+                 log_cap: int = 0, queue_stats=None):
     """Serial simulation of Alg. 1 with p simulated queues (see the C source
-    for the schedule).  Returns (W, H, rec_count, visit_log)."""
+    for the schedule); mode "epoch", "uniform" or "uniform-shorter" (the
+    dynamic load balancing of Sec. 3.3).  Returns (W, H, rec_count,
+    visit_log); `queue_stats`, an int64 array of 2, receives the longest
+    queue met by a push and the sum of the queue lengths met by pushes."""
     W = _c(W, np.float64).copy()
     H = _c(H, np.float64).copy()
     cnt = np.zeros(layout["rec_row"].size, dtype=np.int32)
@@ -274,8 +277,9 @@ def serial_nomad(layout: dict, W, H, lam: float, alpha: float, beta: float,
         W.shape[1], lam, alpha, beta, layout["p"], layout["n"], seg_col.size,
         _ptr(layout["seg_ptr"]), _ptr(seg_col), _ptr(seg_worker), _ptr(rec_row),
         _ptr(rec_val), _ptr(layout["col_seg_ptr"]), _ptr(layout["col_segs"]),
-        n_epochs, seed, {"epoch": 0, "uniform": 1}[mode], _ptr(W), _ptr(H),
-        _ptr(cnt), _ptr(log) if log_cap > 0 else None, log_cap)
+        n_epochs, seed, {"epoch": 0, "uniform": 1, "uniform-shorter": 2}[mode], _ptr(W),
+        _ptr(H), _ptr(cnt), _ptr(log) if log_cap > 0 else None, log_cap,
+        _ptr(queue_stats) if queue_stats is not None else None)
     if nv < 0:
         raise ValueError("serial_nomad: bad argument or corrupt layout")
     return W, H, cnt, log[:min(nv, log_cap)]

@@ -254,6 +254,12 @@ int32_t orc_replay_f32(int32_t k, float lambda, double alpha, double beta,
 /*   queue are uniform over all p workers (streams (seed; j, hop, 1, tag)), */
 /*   a visit to a worker without ratings of j does nothing, and the run     */
 /*   stops once n_epochs * nnz updates have been applied.                   */
+/* mode 2 (uniform with the dynamic load balancing of Sec. 3.3): as mode 1, */
+/*   but every next queue is the shorter of two uniform draws (streams      */
+/*   (seed; j, hop, 1, tag) and (seed; j, hop, 2, tag)), the first one on a */
+/*   tie.                                                                   */
+/* queue_stats (may be NULL): [0] the longest queue met by a push, [1] the  */
+/* sum over pushes of the length of the queue pushed to.                    */
 /*                                                                          */
 /* Workers are served round-robin q = 0,1,...,p-1, each popping at most one */
 /* item per round from the front of its FIFO queue; an empty queue is       */
@@ -271,8 +277,9 @@ int64_t orc_serial_nomad(int32_t k, double lambda, double alpha, double beta,
                          const int64_t *col_segs, int32_t n_epochs,
                          uint64_t seed, int32_t mode, double *W, double *H,
                          int32_t *rec_count, int64_t *visit_log,
-                         int64_t log_cap) {
-  if (p <= 0 || n < 0 || (mode != 0 && mode != 1)) return -1;
+                         int64_t log_cap, int64_t *queue_stats) {
+  if (p <= 0 || n < 0 || mode < 0 || mode > 2) return -1;
+  const int uniform = mode != 0;
   const uint32_t TAG = 0x4f524331u;
   /* FIFO queue per worker, each able to hold all n items. */
   int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(p * (n + 1)));
@@ -288,10 +295,15 @@ int64_t orc_serial_nomad(int32_t k, double lambda, double alpha, double beta,
   int64_t total_nnz = seg_ptr[n_seg];
   int64_t n_visits = 0, n_updates = 0;
 
+  if (queue_stats) queue_stats[0] = queue_stats[1] = 0;
 #define PUSH(q, j)                                                    \
   do {                                                                \
     int64_t pos_ = (qhead[(q)] + qlen[(q)]) % (n + 1);                \
     queue[(int64_t)(q) * (n + 1) + pos_] = (j);                       \
+    if (queue_stats) {                                                \
+      if (qlen[(q)] > queue_stats[0]) queue_stats[0] = qlen[(q)];     \
+      queue_stats[1] += qlen[(q)];                                    \
+    }                                                                 \
     qlen[(q)] += 1;                                                   \
   } while (0)
 
@@ -328,7 +340,7 @@ int64_t orc_serial_nomad(int32_t k, double lambda, double alpha, double beta,
     busy = 0;
     for (int32_t q = 0; q < p; ++q) {
       if (qlen[q] == 0) continue;
-      if (mode == 1 && n_updates >= budget) break;
+      if (uniform && n_updates >= budget) break;
       busy = 1;
       int64_t j = queue[(int64_t)q * (n + 1) + qhead[q]];
       qhead[q] = (qhead[q] + 1) % (n + 1);
@@ -364,10 +376,16 @@ int64_t orc_serial_nomad(int32_t k, double lambda, double alpha, double beta,
       } else {
         hop[j] += 1;
         uint32_t wd = rand_word(seed, (uint32_t)j, (uint32_t)hop[j], 1u, TAG, 1);
-        PUSH((int32_t)bounded(wd, (uint32_t)p), j);
+        int32_t qn = (int32_t)bounded(wd, (uint32_t)p);
+        if (mode == 2) { /* Sec. 3.3: the shorter of two queues */
+          uint32_t wb = rand_word(seed, (uint32_t)j, (uint32_t)hop[j], 2u, TAG, 1);
+          int32_t qb = (int32_t)bounded(wb, (uint32_t)p);
+          if (qlen[qb] < qlen[qn]) qn = qb;
+        }
+        PUSH(qn, j);
       }
     }
-    if (mode == 1 && n_updates >= budget) break;
+    if (uniform && n_updates >= budget) break;
   }
 #undef PUSH
 #undef SHUFFLE

@@ -555,6 +555,7 @@ int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
   TRY(dev_alloc(h, &vp, sizeof(int64_t) * (p + 1))); h->ring_base = (int64_t*)vp;
   TRY(dev_alloc(h, &vp, sizeof(int32_t) * (p + 1))); h->ring_log2 = (int32_t*)vp;
   TRY(dev_alloc(h, &vp, sizeof(uint32_t) * (p + 1))); h->ring_tail = (uint32_t*)vp;
+  TRY(dev_alloc(h, &vp, sizeof(uint32_t) * (p + 1))); h->ring_head = (uint32_t*)vp;
   const int64_t uniform_items = h->sched.mode == NOMAD_MODE_UNIFORM ? n : 0;
   ring_sizes<<<(p + 255) / 256, 256, 0, st>>>(nseg_per_worker, p, uniform_items,
                                               h->ring_log2, caps);

@@ -54,7 +54,7 @@ void free_layout(nomad_handle* h) {
                    (void**)&h->tok_hop,    (void**)&h->tok_epoch, (void**)&h->owner,
                    (void**)&h->rec_count,  (void**)&h->log_seg,   (void**)&h->log_epoch,
                    (void**)&h->item_urgent, (void**)&h->uring,    (void**)&h->uring_tail,
-                   (void**)&h->tok_rec};
+                   (void**)&h->tok_rec,    (void**)&h->ring_head};
   for (void** p : ptrs) dev_free(h, p);
   h->log_cap = 0;
   h->loaded = false;
@@ -159,6 +159,7 @@ void nomad_schedule_default(nomad_schedule* s) {
   s->device = 0;
   s->debug_drop_item = -1;
   s->variant = NOMAD_VARIANT_BATCHED;
+  s->routing = NOMAD_ROUTING_UNIFORM;
 }
 
 const char* nomad_error_string(int32_t code) {
@@ -193,7 +194,8 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
       (sched.mode != NOMAD_MODE_EPOCH && sched.mode != NOMAD_MODE_UNIFORM) ||
       (sched.partition != NOMAD_PARTITION_RATINGS && sched.partition != NOMAD_PARTITION_USERS) ||
       sched.n_workers < 0 || sched.warps_per_block < 0 || sched.spin_timeout_ns < 0 ||
-      (sched.variant != NOMAD_VARIANT_BATCHED && sched.variant != NOMAD_VARIANT_SIMPLE))
+      (sched.variant != NOMAD_VARIANT_BATCHED && sched.variant != NOMAD_VARIANT_SIMPLE) ||
+      (sched.routing != NOMAD_ROUTING_UNIFORM && sched.routing != NOMAD_ROUTING_SHORTER))
     return NOMAD_ERR_INVALID_ARG;
   if (sched.precision != NOMAD_FP32 && sched.precision != NOMAD_BF16) return NOMAD_ERR_INVALID_ARG;
   if (sched.precision == NOMAD_BF16 &&

@@ -76,6 +76,14 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(
 __device__ __forceinline__ void fence_acq_rel_gpu() {
   asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ int ld_relaxed_i32(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -108,6 +116,8 @@ struct SgdParams {
   const int64_t* ring_base; // p
   const int32_t* ring_log2; // p: log2 of the ring capacity
   uint32_t* ring_tail;      // p: producer reservation counters
+  uint32_t* ring_head;      // p: tokens taken so far (uniform mode), written by the owner
+  int32_t routing;          // uniform mode: NOMAD_ROUTING_*
   unsigned long long* uring;  // p x 2^uring_log2 slots: tokens of urgent items
   uint32_t* uring_tail;       // p
   int32_t uring_log2;
@@ -191,6 +201,7 @@ struct nomad_handle {
   int64_t* ring_base = nullptr;
   int32_t* ring_log2 = nullptr;
   uint32_t* ring_tail = nullptr;
+  uint32_t* ring_head = nullptr;  // p: tokens taken (uniform mode, load-balanced routing)
   unsigned long long* uring = nullptr;  // per worker: tokens of urgent items
   uint32_t* uring_tail = nullptr;
   int32_t uring_log2 = 0;

@@ -260,6 +260,8 @@ nomad_uniform_kernel(const SgdParams P) {
     int j = 0, hop = 0;
     if (lane == 0) {
       j = pop_token(P, q, head, lg, ring_q);
+      // tokens taken, for senders that route to the shorter queue
+      if (j >= 0 && P.routing == NOMAD_ROUTING_SHORTER) st_relaxed_u32(P.ring_head + q, head + 1);
       if (j >= 0) {
         hop = __ldcg(P.tok_hop + j);
         if (DEBUG && atomicExch(P.owner + j, q) != -1) flag_ownership(P, q, j);
@@ -325,7 +327,15 @@ nomad_uniform_kernel(const SgdParams P) {
       __stcg(P.tok_hop + j, nh);
       if (DEBUG && atomicExch(P.owner + j, -1) != q) flag_ownership(P, q, j);
       const uint4 r = philox4x32_10(make_uint4(uint32_t(j), uint32_t(nh), 0u, kTagUniform), seed);
-      const int q2 = int((static_cast<unsigned long long>(r.x) * uint32_t(P.p)) >> 32);
+      int q2 = int((static_cast<unsigned long long>(r.x) * uint32_t(P.p)) >> 32);
+      if (P.routing == NOMAD_ROUTING_SHORTER) {
+        // Sec. 3.3: of two workers drawn uniformly, the one with fewer tokens
+        // waiting (pushed minus taken; a snapshot, as a message payload is)
+        const int qb = int((static_cast<unsigned long long>(r.y) * uint32_t(P.p)) >> 32);
+        const uint32_t la = ld_relaxed_u32(P.ring_tail + q2) - ld_relaxed_u32(P.ring_head + q2);
+        const uint32_t lb = ld_relaxed_u32(P.ring_tail + qb) - ld_relaxed_u32(P.ring_head + qb);
+        if (lb < la) q2 = qb;
+      }
       __threadfence();
       push_token(P, q2, uint32_t(j));
     }
@@ -416,6 +426,8 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   P.ring_base = h->ring_base;
   P.ring_log2 = h->ring_log2;
   P.ring_tail = h->ring_tail;
+  P.ring_head = h->ring_head;
+  P.routing = h->sched.routing;
   P.tok_hop = h->tok_hop;
   P.tok_epoch = h->tok_epoch;
   P.item_urgent = h->item_urgent;
@@ -451,6 +463,7 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->ring, 0xff, sizeof(unsigned long long) * h->ring_slots, st)) ||
       (e = cudaMemsetAsync(h->ring_tail, 0, sizeof(uint32_t) * h->p, st)) ||
+      (e = cudaMemsetAsync(h->ring_head, 0, sizeof(uint32_t) * h->p, st)) ||
       (h->uring && (e = cudaMemsetAsync(h->uring, 0xff,
                                         sizeof(unsigned long long) * (int64_t(h->p) << h->uring_log2),
                                         st))) ||

@@ -301,16 +301,19 @@ def test_free_run_large_steps_within_order_spread(tiny):
 
 
 # ---------------------------------------------------------------- uniform mode
-@pytest.mark.parametrize("p", [16, 64])
-def test_uniform_mode_replay_and_budget(tiny, p):
-    """Alg. 1 literally: the next worker is uniform over all p, a visit to a
-    worker without ratings of the item applies nothing, the per-rating update
-    count gives t, and a call stops after n_epochs * nnz updates.  The logged
-    order of non-empty visits replays to the same factors on the oracle."""
+@pytest.mark.parametrize("p,routing", [(16, "uniform"), (64, "uniform"), (16, "shorter"),
+                                       (64, "shorter")])
+def test_uniform_mode_replay_and_budget(tiny, p, routing):
+    """Alg. 1 literally: the next worker is uniform over all p (or, with the
+    dynamic load balancing of Sec. 3.3, the one of two uniform draws with
+    fewer tokens waiting), a visit to a worker without ratings of the item
+    applies nothing, the per-rating update count gives t, and a call stops
+    after n_epochs * nnz updates.  The logged order of non-empty visits
+    replays to the same factors on the oracle."""
     tr, tc, tv, *_ = tiny.numpy()
     a32, b32, lam32 = (float(np.float32(x)) for x in (0.05, 0.05, 0.05))
     with make(tiny, 10, 0.05, alpha=0.05, beta=0.05, mode="uniform", debug=True,
-              n_workers=p) as nm:
+              n_workers=p, routing=routing) as nm:
         L, _ = oracle_layout(nm, tiny)
         W0, H0 = nm.factors()
         nm.epoch(2)

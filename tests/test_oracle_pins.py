@@ -319,6 +319,31 @@ def test_serial_nomad_accounting(mode):
     assert np.array_equal(cnt, cnt2)
 
 
+def test_shorter_queue_routing_balances_the_queues():
+    """Sec. 3.3: sending each token to the shorter of two uniformly drawn
+    queues keeps the longest queue shorter than uniform routing (Alg. 1)
+    does on the same draws, and the run still applies n_epochs * nnz
+    updates whose logged order replays to the same factors."""
+    r, (tr, tc, tv, *_), L = _tiny()
+    k, E = 10, 3
+    W0 = oracle.init_factor(r.m, k, 2, 0)
+    H0 = oracle.init_factor(r.n, k, 2, 1)
+    out = {}
+    for mode in ("uniform", "uniform-shorter"):
+        st = np.zeros(2, dtype=np.int64)
+        W, H, cnt, log = oracle.serial_nomad(L, W0, H0, 0.05, 0.012, 0.05, E, 3, mode=mode,
+                                             log_cap=10 ** 7, queue_stats=st)
+        assert E * tr.size <= cnt.sum() < E * tr.size + 1000
+        valid = log[log >= 0]
+        W2, H2, cnt2 = oracle.replay(L, valid, W0, H0, 0.05, 0.012, 0.05)
+        assert np.array_equal(W, W2) and np.array_equal(H, H2)
+        out[mode] = (st.copy(), log.size)
+    (su, nu), (ss, ns) = out["uniform"], out["uniform-shorter"]
+    # the longest queue met by a push (the mean is n/p either way: every
+    # token is always in some queue)
+    assert ss[0] < 0.75 * su[0], (ss, su)
+
+
 def test_serializability_commuting_visits():
     """Visits that share neither worker nor item touch disjoint variables, so
     swapping two adjacent such visits leaves the replay result bit-identical
