@@ -65,15 +65,6 @@ void free_layout(nomad_handle* h) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-bool is_device_pointer(const void* p) {
-  cudaPointerAttributes a{};
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 // Device copy of a caller array: the array itself when it already is device
 // memory, else a stream-ordered temporary filled from the host.
 template <typename T>
@@ -236,22 +227,21 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
 
   const size_t esz = size_t(h->elem);
   void* vp = nullptr;
-  cudaError_t e;
-  if ((e = dev_alloc(h, &vp, esz * size_t(m) * h->pitch)) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, esz * size_t(m) * h->pitch) != cudaSuccess) goto oom;
   h->W = vp;
-  if ((e = dev_alloc(h, &vp, esz * size_t(n) * h->pitch)) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, esz * size_t(n) * h->pitch) != cudaSuccess) goto oom;
   h->H = vp;
-  if ((e = dev_alloc(h, &vp, sizeof(int32_t) * kStatusWords)) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, sizeof(int32_t) * kStatusWords) != cudaSuccess) goto oom;
   h->status = static_cast<int32_t*>(vp);
-  if ((e = dev_alloc(h, &vp, sizeof(int32_t) * size_t(m))) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, sizeof(int32_t) * size_t(m)) != cudaSuccess) goto oom;
   h->row_worker = static_cast<int32_t*>(vp);
-  if ((e = dev_alloc(h, &vp, sizeof(double) * 2)) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, sizeof(double) * 2) != cudaSuccess) goto oom;
   h->result = static_cast<double*>(vp);
-  if ((e = dev_alloc(h, &vp, sizeof(unsigned long long) * 2)) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, sizeof(unsigned long long) * 2) != cudaSuccess) goto oom;
   h->upd_done = static_cast<unsigned long long*>(vp);
-  if ((e = dev_alloc(h, &vp, sizeof(int32_t) * 2)) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, sizeof(int32_t) * 2) != cudaSuccess) goto oom;
   h->stop = static_cast<int32_t*>(vp);
-  if ((e = dev_alloc(h, &vp, sizeof(uint32_t) * 2)) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, sizeof(uint32_t) * 2) != cudaSuccess) goto oom;
   h->log_ticket = static_cast<uint32_t*>(vp);
   if (cudaMemset(h->status, 0, sizeof(int32_t) * kStatusWords) != cudaSuccess) goto cuda_err;
   if (cudaMemset(h->W, 0, esz * size_t(m) * h->pitch) != cudaSuccess) goto cuda_err;
@@ -282,7 +272,7 @@ int nomad_load_ratings(nomad_t* h, int32_t fmt, int64_t nnz, const void* major,
   free_layout(h);
   const int32_t *d_rows = nullptr, *d_cols = nullptr;
   const float* d_vals = nullptr;
-  int32_t *own_rows = nullptr, *own_cols = nullptr, *own_major = nullptr;
+  int32_t *own_rows = nullptr, *own_cols = nullptr;
   float* own_vals = nullptr;
   int64_t* own_colptr = nullptr;
   int32_t* exp_cols = nullptr;
@@ -310,7 +300,6 @@ int nomad_load_ratings(nomad_t* h, int32_t fmt, int64_t nnz, const void* major,
     CK(h, cudaStreamSynchronize(st), "load_ratings");
     if (status != 0) rc = fail(h, NOMAD_ERR_INVALID_ARG, "load_ratings: bad column pointers");
     d_cols = exp_cols;
-    (void)own_major;
   }
   if (rc == NOMAD_OK)
     CK(h, stage<float>(vals, nnz, device_ptrs, st, &d_vals, &own_vals), "load_ratings: vals");
