@@ -5,7 +5,7 @@
 // circulation of Sec. 3.4), organised so that the latency of global memory is
 // paid per batch of tokens instead of per visit:
 //
-//  1. take the ready prefix of the own ring (up to kBatch tokens) with one
+//  1. take the ready prefix of the own ring (up to Batch<CPL> tokens) with one
 //     acquire load per lane;
 //  2. fetch every token's metadata lane-parallel (lane b = token b);
 //  3. order the visits: long visits (>= kHeavy ratings, the items whose
@@ -31,7 +31,10 @@
 namespace nomad {
 namespace {
 
-constexpr int kBatch = 8;      // tokens taken from the ring at once
+// Tokens taken from the ring at once: 16 when a row is one 16-byte chunk per
+// lane, 8 otherwise (shared memory holds their h).
+template <int CPL>
+constexpr int Batch = CPL == 1 ? 16 : 8;
 constexpr int kRecBuf = 128;   // circular buffer of record positions
 constexpr int kRecInit = 64;   // positions loaded before the first row copy
 constexpr int kHeavy = 32;     // visits this long go first and are pushed at once
@@ -40,15 +43,16 @@ constexpr int kStreamChunks = 16;  // row-ring chunks per lane of the generic st
 constexpr int kBatchedWarps = 8;   // warps per thread block at most (register budget)
 
 constexpr int kVisitChunks = 21;   // ring chunks of a long visit at one chunk per lane
+constexpr int kUrgentChunks = 14;  // ring chunks of a visit taken out of turn
 
 // Row ring per lane: CHUNKS 16-byte chunks.  The generic stream uses the
 // first kStreamChunks and a long visit of the batch the first VISIT (each
 // runs alone); at one chunk per lane a visit of an urgent item that
-// interrupts either of them uses the kVisitChunks after those.
+// interrupts either of them uses the kUrgentChunks after those.
 template <int CPL>
 struct RowRing {
   static constexpr int VISIT = CPL == 1 ? kVisitChunks : kStreamChunks;
-  static constexpr int CHUNKS = CPL == 1 ? 2 * kVisitChunks : kStreamChunks;
+  static constexpr int CHUNKS = CPL == 1 ? kVisitChunks + kUrgentChunks : kStreamChunks;
   static constexpr int R = kStreamChunks / CPL;  // slots; R-1 rows in flight
   static_assert(kStreamChunks <= VISIT, "the stream's slots lie in the batch's region");
 };
@@ -92,8 +96,9 @@ __device__ __forceinline__ uint2 pack_sr(float4 v, uint32_t ra, uint32_t rb) {
 // (int2) and two int4 tables of batch metadata.
 template <int CPL, bool BF>
 __host__ __device__ constexpr int warp_smem_bytes() {
-  return int((RowRing<CPL>::CHUNKS + kBatch * CPL) * 32 * sizeof(typename Storage<BF>::chunk_t)) +
-         kRecBuf * 8 + 2 * kBatch * 16;
+  return int((RowRing<CPL>::CHUNKS + Batch<CPL> * CPL) * 32 *
+             sizeof(typename Storage<BF>::chunk_t)) +
+         kRecBuf * 8 + 2 * Batch<CPL> * 16;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -114,12 +119,13 @@ __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;
 // Copies the records of stream positions [p0, p0 + count) (count <= 32) into
 // the circular buffer.  Lane r < nb holds the stream offset `soff` and first
 // record `beg` of the rank-r visit (offsets increase with the rank).
+template <int KB>
 __device__ __forceinline__ void load_records(int2* recs, const int2* __restrict__ rec, int soff,
                                              int64_t beg, int nb, int p0, int count, int lane) {
   const int p = p0 + lane;
   int r = 0;  // the visit of position p: the last rank whose offset is <= p
 #pragma unroll
-  for (int i = 1; i < kBatch; ++i) {
+  for (int i = 1; i < KB; ++i) {
     const int o = __shfl_sync(kFull, soff, i);
     if (i < nb && o <= p) r = i;
   }
@@ -393,7 +399,7 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
     }
     if (atomicExch(P.owner + uj, q) != -1) flag_ownership(P, q, uj);
   }
-  long_visit<1, BF, DEBUG, kVisitChunks>(uh, rows, W4, pitch4, k4, P.rec, ubeg, uc, us,
+  long_visit<1, BF, DEBUG, kUrgentChunks>(uh, rows, W4, pitch4, k4, P.rec, ubeg, uc, us,
                                          P.lambda, ue, seed, lane, P.rec_count);
   if (lane < k4) {
     if constexpr (BF) {
@@ -428,6 +434,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
   chunk_t* rows = reinterpret_cast<chunk_t*>(reinterpret_cast<unsigned char*>(smem_f4) +
                                              size_t(wib) * warp_smem_bytes<CPL, BF>());
   chunk_t* hbuf = rows + RowRing<CPL>::CHUNKS * 32;
+  constexpr int kBatch = Batch<CPL>;
   int2* recs = reinterpret_cast<int2*>(hbuf + kBatch * CPL * 32);
   int4* meta_a = reinterpret_cast<int4*>(recs + kRecBuf);  // {j, c, e, seg}
   int4* meta_b = meta_a + kBatch;                          // {beg_lo, beg_hi, lane, soff}
@@ -604,7 +611,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
     for (int r = 0; r < nhv; ++r) T0 += meta_a[r].y;
     int loaded = T - T0 < kRecInit ? T : T0 + kRecInit;
     for (int p0 = T0; p0 < loaded; p0 += 32)
-      load_records(recs, P.rec, v_soff, v_beg, nb, p0, loaded - p0 < 32 ? loaded - p0 : 32,
+      load_records<kBatch>(recs, P.rec, v_soff, v_beg, nb, p0, loaded - p0 < 32 ? loaded - p0 : 32,
                    lane);
     cp_commit();
 
@@ -777,7 +784,7 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
       // keep the records one chunk ahead of the row prefetch
       if (loaded < T && loaded < t + R + 32) {
         const int cnt = T - loaded < 32 ? T - loaded : 32;
-        load_records(recs, P.rec, v_soff, v_beg, nb, loaded, cnt, lane);
+        load_records<kBatch>(recs, P.rec, v_soff, v_beg, nb, loaded, cnt, lane);
         loaded += cnt;
       }
       const int pp = t + R - 1;
