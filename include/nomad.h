@@ -73,7 +73,7 @@ extern "C" {
 #define NOMAD_PARTITION_USERS 1   /* blocks with equal numbers of users
                                      (Sec. 3.1) */
 
-#define NOMAD_VARIANT_BATCHED 0 /* a worker takes up to 8 ready tokens at once,
+#define NOMAD_VARIANT_BATCHED 0 /* a worker takes up to 16 ready tokens at once,
                                    streams W rows through shared memory
                                    (default) */
 #define NOMAD_VARIANT_SIMPLE 1  /* a worker handles one token at a time */
@@ -166,6 +166,28 @@ NOMAD_API int nomad_load_ratings(nomad_t *h, int32_t fmt, int64_t nnz, const voi
  * are reported by the next nomad_check / nomad_rmse / nomad_objective /
  * nomad_get_factors call. */
 NOMAD_API int nomad_epoch(nomad_t *h, int32_t n_epochs, void *stream);
+
+/* nomad_epoch for `count` independent problems at once: one persistent
+ * launch in which each problem runs on its own blocks (h[g]->n_workers
+ * workers, i.e. its schedule's n_workers / warps_per_block blocks), as in a
+ * sweep over lambda, k or data (App. A/B).  The problems share no data; each
+ * one's updates, visit order, replay log and errors are those nomad_epoch
+ * would give with the same workers.
+ *  - h: `count` distinct loaded handles on the same device, all in
+ *    NOMAD_MODE_EPOCH with NOMAD_VARIANT_BATCHED, the same precision, the
+ *    same debug flag, the same warps_per_block and the same row width class
+ *    (k <= 128, k <= 256 or k <= 512); the caller keeps the array.
+ *  - Their blocks together must fit on the device at once (one block of
+ *    warps_per_block warps per SM with the default shared memory use):
+ *    otherwise NOMAD_ERR_UNSUPPORTED and nothing runs.
+ *  - Asynchronous on `stream`; per-handle errors as for nomad_epoch, and
+ *    nomad_last_epoch_kernel_ms of every handle reports the one launch.
+ * Errors: NOMAD_ERR_INVALID_ARG (count < 1, a NULL or repeated handle,
+ * n_epochs < 1), NOMAD_ERR_STATE (a handle without ratings),
+ * NOMAD_ERR_UNSUPPORTED (handles that differ in the above, or too many
+ * blocks). */
+NOMAD_API int nomad_epoch_many(nomad_t *const *h, int32_t count, int32_t n_epochs,
+                               void *stream);
 
 /* Wait for the handle's work on `stream` and report any device-side error
  * of earlier nomad_epoch calls (then clears it). */

@@ -421,18 +421,14 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
   if (lane == 0 && unseg >= 0) push_urgent(P, uq2, uint32_t(uj));
 }
 
+// Worker q of the problem P (one warp), with its shared memory at `wsmem`
+// (warp_smem_bytes<CPL, BF>() bytes).
 template <int CPL, bool BF, bool DEBUG>
-__global__ void __launch_bounds__(kBatchedWarps * 32, 1)
-nomad_batched_kernel(const __grid_constant__ SgdParams P) {
+__device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsigned char* wsmem) {
   constexpr int R = RowRing<CPL>::R;
   using chunk_t = typename Storage<BF>::chunk_t;
-  extern __shared__ float4 smem_f4[];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int q = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (q >= P.p) return;
-  chunk_t* rows = reinterpret_cast<chunk_t*>(reinterpret_cast<unsigned char*>(smem_f4) +
-                                             size_t(wib) * warp_smem_bytes<CPL, BF>());
+  chunk_t* rows = reinterpret_cast<chunk_t*>(wsmem);
   chunk_t* hbuf = rows + RowRing<CPL>::CHUNKS * 32;
   constexpr int kBatch = Batch<CPL>;
   int2* recs = reinterpret_cast<int2*>(hbuf + kBatch * CPL * 32);
@@ -880,23 +876,63 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
   }
 }
 
+template <int CPL, bool BF, bool DEBUG>
+__global__ void __launch_bounds__(kBatchedWarps * 32, 1)
+nomad_batched_kernel(const __grid_constant__ SgdParams P) {
+  extern __shared__ float4 smem_f4[];
+  const int wib = threadIdx.x >> 5;
+  const int q = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (q >= P.p) return;
+  batched_worker<CPL, BF, DEBUG>(P, q, reinterpret_cast<unsigned char*>(smem_f4) +
+                                           size_t(wib) * warp_smem_bytes<CPL, BF>());
+}
+
+// Several independent problems in one launch: block b runs block
+// `blocks[b].y` of problem `blocks[b].x`, whose parameters (Ps[blocks[b].x])
+// are copied into shared memory after the warps' areas.  Every block of a
+// problem is resident with the others (cooperative launch), as in the
+// one-problem kernel; problems share nothing.
+template <int CPL, bool BF, bool DEBUG>
+__global__ void __launch_bounds__(kBatchedWarps * 32, 1)
+nomad_batched_many_kernel(const SgdParams* __restrict__ Ps, const int2* __restrict__ blocks) {
+  extern __shared__ float4 smem_f4[];
+  const int nw = blockDim.x >> 5;
+  unsigned char* base = reinterpret_cast<unsigned char*>(smem_f4);
+  SgdParams* Pb = reinterpret_cast<SgdParams*>(base + size_t(nw) * warp_smem_bytes<CPL, BF>());
+  const int2 bp = blocks[blockIdx.x];
+  const int* src = reinterpret_cast<const int*>(Ps + bp.x);
+  int* dst = reinterpret_cast<int*>(Pb);
+  for (int i = threadIdx.x; i < int(sizeof(SgdParams) / sizeof(int)); i += blockDim.x)
+    dst[i] = src[i];
+  __syncthreads();
+  const int wib = threadIdx.x >> 5;
+  const int q = bp.y * nw + wib;
+  if (q >= Pb->p) return;
+  batched_worker<CPL, BF, DEBUG>(*Pb, q, base + size_t(wib) * warp_smem_bytes<CPL, BF>());
+}
+
 template <int CPL, bool BF>
-const void* batched_ptr(bool debug, size_t* smem_per_warp) {
+const void* batched_ptr(bool debug, bool many, size_t* smem_per_warp) {
   *smem_per_warp = size_t(warp_smem_bytes<CPL, BF>());
+  if (many)
+    return debug ? (const void*)nomad_batched_many_kernel<CPL, BF, true>
+                 : (const void*)nomad_batched_many_kernel<CPL, BF, false>;
   return debug ? (const void*)nomad_batched_kernel<CPL, BF, true>
                : (const void*)nomad_batched_kernel<CPL, BF, false>;
 }
 
 }  // namespace
 
-// Kernel pointer and per-warp shared memory (bytes) of the batched kernel.
-const void* batched_kernel(int k4, bool debug, bool bf16, size_t* smem_per_warp) {
-  if (k4 <= 32) return bf16 ? batched_ptr<1, true>(debug, smem_per_warp)
-                            : batched_ptr<1, false>(debug, smem_per_warp);
-  if (k4 <= 64) return bf16 ? batched_ptr<2, true>(debug, smem_per_warp)
-                            : batched_ptr<2, false>(debug, smem_per_warp);
-  if (k4 <= 128) return bf16 ? batched_ptr<4, true>(debug, smem_per_warp)
-                             : batched_ptr<4, false>(debug, smem_per_warp);
+// Kernel pointer and per-warp shared memory (bytes) of the batched kernel,
+// or of its several-problem form (`many`, which also takes sizeof(SgdParams)
+// bytes per block).
+const void* batched_kernel(int k4, bool debug, bool bf16, bool many, size_t* smem_per_warp) {
+  if (k4 <= 32) return bf16 ? batched_ptr<1, true>(debug, many, smem_per_warp)
+                            : batched_ptr<1, false>(debug, many, smem_per_warp);
+  if (k4 <= 64) return bf16 ? batched_ptr<2, true>(debug, many, smem_per_warp)
+                            : batched_ptr<2, false>(debug, many, smem_per_warp);
+  if (k4 <= 128) return bf16 ? batched_ptr<4, true>(debug, many, smem_per_warp)
+                             : batched_ptr<4, false>(debug, many, smem_per_warp);
   return nullptr;
 }
 

@@ -320,14 +320,16 @@ int nomad_load_ratings(nomad_t* h, int32_t fmt, int64_t nnz, const void* major,
   return NOMAD_OK;
 }
 
-int nomad_epoch(nomad_t* h, int32_t n_epochs, void* stream) {
-  if (!h) return NOMAD_ERR_INVALID_ARG;
+namespace {
+
+// Checks of one handle before n_epochs epochs, and its per-call buffers (the
+// step-size table, the replay log) grown to the call's size.  The caller
+// has made the handle's device current.
+int prepare_call(nomad_t* h, int32_t n_epochs) {
   if (!h->loaded) return fail(h, NOMAD_ERR_STATE, "epoch: no ratings loaded");
   if (n_epochs < 1) return fail(h, NOMAD_ERR_INVALID_ARG, "epoch: n_epochs < 1");
   if (h->epochs_done + n_epochs >= (int64_t(1) << 31))
     return fail(h, NOMAD_ERR_INVALID_ARG, "epoch: epoch counter overflow");
-  DeviceGuard guard(h->device);
-  cudaStream_t st = as_stream(stream);
   void* vp = nullptr;
   if (h->sched.mode == NOMAD_MODE_EPOCH && h->step_cap < n_epochs) {
     vp = h->step;
@@ -356,9 +358,67 @@ int nomad_epoch(nomad_t* h, int32_t n_epochs, void* stream) {
       h->log_cap = need;
     }
   }
-  const int rc = launch_epochs(h, n_epochs, st);
+  return NOMAD_OK;
+}
+
+// An error of handle h in a call over several handles, reported on h and on
+// the first handle of the call.
+int fail_many(nomad_t* h0, nomad_t* h, int code, const std::string& msg) {
+  if (h != h0) fail(h0, code, msg);
+  return fail(h, code, msg);
+}
+
+// Row width class of the batched kernel: one, two or four 16-byte chunks
+// per lane.
+int width_class(const nomad_t* h) { return h->k4 <= 32 ? 1 : h->k4 <= 64 ? 2 : 4; }
+
+}  // namespace
+
+int nomad_epoch(nomad_t* h, int32_t n_epochs, void* stream) {
+  if (!h) return NOMAD_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  cudaStream_t st = as_stream(stream);
+  int rc = prepare_call(h, n_epochs);
+  if (rc != NOMAD_OK) return rc;
+  rc = launch_epochs(h, n_epochs, st);
   if (rc != NOMAD_OK) return rc;
   h->epochs_done += n_epochs;
+  return NOMAD_OK;
+}
+
+int nomad_epoch_many(nomad_t* const* hs, int32_t count, int32_t n_epochs, void* stream) {
+  if (!hs || count < 1) return NOMAD_ERR_INVALID_ARG;
+  for (int g = 0; g < count; ++g) {
+    if (!hs[g]) return NOMAD_ERR_INVALID_ARG;
+    for (int f = 0; f < g; ++f)
+      if (hs[f] == hs[g]) return fail_many(hs[0], hs[g], NOMAD_ERR_INVALID_ARG, "epoch_many: a handle occurs twice");
+  }
+  nomad_t* h0 = hs[0];
+  for (int g = 0; g < count; ++g) {
+    nomad_t* h = hs[g];
+    if (!h->loaded) return fail_many(h0, h, NOMAD_ERR_STATE, "epoch_many: no ratings loaded");
+    if (h->sched.mode != NOMAD_MODE_EPOCH || h->sched.variant != NOMAD_VARIANT_BATCHED)
+      return fail_many(h0, h, NOMAD_ERR_UNSUPPORTED,
+                       "epoch_many: epoch mode with the batched variant only");
+    if (h->device != h0->device || h->sched.precision != h0->sched.precision ||
+        (h->sched.debug != 0) != (h0->sched.debug != 0) ||
+        h->warps_per_block != h0->warps_per_block || width_class(h) != width_class(h0))
+      return fail_many(h0, h, NOMAD_ERR_UNSUPPORTED,
+                       "epoch_many: handles differ in device, precision, debug, warps per block or "
+                  "row width");
+  }
+  DeviceGuard guard(h0->device);
+  cudaStream_t st = as_stream(stream);
+  for (int g = 0; g < count; ++g) {
+    const int rc = prepare_call(hs[g], n_epochs);
+    if (rc != NOMAD_OK) {
+      if (hs[g] != h0) h0->last_error = hs[g]->last_error;
+      return rc;
+    }
+  }
+  const int rc = launch_epochs_many(hs, count, n_epochs, st);
+  if (rc != NOMAD_OK) return rc;
+  for (int g = 0; g < count; ++g) hs[g]->epochs_done += n_epochs;
   return NOMAD_OK;
 }
 

@@ -246,12 +246,13 @@ int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
 
 // Persistent SGD kernel launch (sgd.cu).
 int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t stream);
+int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cudaStream_t stream);
 int max_resident_workers(int device, int warps_per_block, int k4, int precision,
                          int mode, int variant, int* blocks_per_sm);
 int default_warps_per_block();
 // Batched epoch-mode worker kernel (epoch_batched.cu): pointer and dynamic
 // shared memory per warp in bytes; nullptr for an unsupported k4.
-const void* batched_kernel(int k4, bool debug, bool bf16, size_t* smem_per_warp);
+const void* batched_kernel(int k4, bool debug, bool bf16, bool many, size_t* smem_per_warp);
 
 // Initialisation, evaluation and factor copies (eval.cu).
 int init_factors(nomad_handle* h, cudaStream_t stream);

@@ -370,7 +370,7 @@ const void* worker_kernel(int k4, bool debug, int mode, int variant, int precisi
                           size_t* smem_per_warp) {
   *smem_per_warp = 0;
   if (mode == NOMAD_MODE_EPOCH && variant == NOMAD_VARIANT_BATCHED)
-    return batched_kernel(k4, debug, precision == NOMAD_BF16, smem_per_warp);
+    return batched_kernel(k4, debug, precision == NOMAD_BF16, false, smem_per_warp);
   if (precision != NOMAD_FP32) return nullptr;  // bfloat16 storage: batched kernel only
   if (k4 <= 32) return epoch_kernel_ptr<1>(debug, mode);
   if (k4 <= 64) return epoch_kernel_ptr<2>(debug, mode);
@@ -407,10 +407,16 @@ int max_resident_workers(int device, int warps_per_block, int k4, int precision,
 
 int default_warps_per_block() { return kDefaultWarpsPerBlock; }
 
-int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
+namespace {
+
+// The worker kernel's parameters for the next n_epochs of handle h (in *out),
+// after the launch's preparation on `st`: ring, queue and status resets, the
+// step-size table and the initial tokens.
+int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams* out) {
   const bool uniform = h->sched.mode == NOMAD_MODE_UNIFORM;
   const bool debug = h->sched.debug != 0;
-  SgdParams P{};
+  SgdParams& P = *out;
+  P = SgdParams{};
   P.W = h->W;
   P.H = h->H;
   P.pitch = h->pitch;
@@ -486,13 +492,6 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   if (seed_grid < 1) seed_grid = 1;
   seed_tokens<<<seed_grid, 256, 0, st>>>(P, n);
   ++h->launches;
-  if (h->nnz == 0) return NOMAD_OK;
-
-  size_t spw = 0;
-  const void* fn = worker_kernel(h->k4, debug, h->sched.mode, h->sched.variant,
-                                 h->sched.precision, &spw);
-  const size_t smem = spw * size_t(h->warps_per_block);
-  void* args[] = {&P};
   if (!h->ev_start) {
     if (cudaEventCreate(&h->ev_start) != cudaSuccess ||
         cudaEventCreate(&h->ev_stop) != cudaSuccess) {
@@ -500,6 +499,22 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
       return NOMAD_ERR_CUDA;
     }
   }
+  return NOMAD_OK;
+}
+
+}  // namespace
+
+int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
+  SgdParams P{};
+  const int rc = prepare_epochs(h, n_epochs, st, &P);
+  if (rc != NOMAD_OK || h->nnz == 0) return rc;
+  const bool debug = h->sched.debug != 0;
+  size_t spw = 0;
+  const void* fn = worker_kernel(h->k4, debug, h->sched.mode, h->sched.variant,
+                                 h->sched.precision, &spw);
+  const size_t smem = spw * size_t(h->warps_per_block);
+  void* args[] = {&P};
+  cudaError_t e;
   cudaEventRecord(h->ev_start, st);
   e = cudaLaunchCooperativeKernel(fn, dim3(h->blocks), dim3(h->warps_per_block * 32), args,
                                   smem, st);
@@ -510,6 +525,83 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   ++h->launches;
   cudaEventRecord(h->ev_stop, st);
   h->ev_recorded = true;
+  return NOMAD_OK;
+}
+
+// Several handles' epochs in one launch of the batched kernel's several-
+// problem form: handle g's blocks run its workers with its own parameters
+// (copied to the device for the launch).  The caller has checked that the
+// handles agree in mode, variant, precision, debug flag, warps per block and
+// row width class.
+int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cudaStream_t st) {
+  nomad_handle* h0 = hs[0];
+  const bool debug = h0->sched.debug != 0;
+  const int wpb = h0->warps_per_block;
+  size_t spw = 0;
+  const void* fn = batched_kernel(h0->k4, debug, h0->sched.precision == NOMAD_BF16, true, &spw);
+  if (!fn) return NOMAD_ERR_UNSUPPORTED;
+  const size_t smem = spw * size_t(wpb) + ((sizeof(SgdParams) + 15) & ~size_t(15));
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+          cudaSuccess) {
+    h0->last_error = "epoch_many: shared memory per block exceeds the device limit";
+    return NOMAD_ERR_UNSUPPORTED;
+  }
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h0->device) != cudaSuccess) {
+    h0->last_error = "epoch_many: occupancy query failed";
+    return NOMAD_ERR_CUDA;
+  }
+  int64_t total = 0;
+  for (int g = 0; g < count; ++g)
+    if (hs[g]->nnz > 0) total += hs[g]->blocks;
+  if (total > int64_t(per_sm) * sms) {
+    h0->last_error = "epoch_many: " + std::to_string(total) + " blocks do not fit on the device at once (" +
+                     std::to_string(int64_t(per_sm) * sms) + ")";
+    return NOMAD_ERR_UNSUPPORTED;
+  }
+  std::vector<SgdParams> Ps;
+  std::vector<int2> blocks;
+  Ps.reserve(size_t(count));
+  for (int g = 0; g < count; ++g) {
+    SgdParams P{};
+    const int rc = prepare_epochs(hs[g], n_epochs, st, &P);
+    if (rc != NOMAD_OK) {
+      if (hs[g] != h0) h0->last_error = hs[g]->last_error;
+      return rc;
+    }
+    if (hs[g]->nnz == 0) continue;
+    for (int b = 0; b < hs[g]->blocks; ++b) blocks.push_back(make_int2(int(Ps.size()), b));
+    Ps.push_back(P);
+  }
+  if (blocks.empty()) return NOMAD_OK;
+  void* dP = nullptr;
+  void* dB = nullptr;
+  cudaError_t e = cudaMallocAsync(&dP, sizeof(SgdParams) * Ps.size(), st);
+  if (!e) e = cudaMallocAsync(&dB, sizeof(int2) * blocks.size(), st);
+  if (!e) e = cudaMemcpyAsync(dP, Ps.data(), sizeof(SgdParams) * Ps.size(), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(dB, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice, st);
+  if (!e) {
+    for (int g = 0; g < count; ++g) cudaEventRecord(hs[g]->ev_start, st);
+    const SgdParams* aP = static_cast<const SgdParams*>(dP);
+    const int2* aB = static_cast<const int2*>(dB);
+    void* args[] = {&aP, &aB};
+    e = cudaLaunchCooperativeKernel(fn, dim3(unsigned(blocks.size())), dim3(wpb * 32), args, smem, st);
+    if (!e) {
+      ++h0->launches;
+      for (int g = 0; g < count; ++g) {
+        cudaEventRecord(hs[g]->ev_stop, st);
+        hs[g]->ev_recorded = true;
+      }
+    }
+  }
+  if (dP) cudaFreeAsync(dP, st);
+  if (dB) cudaFreeAsync(dB, st);
+  if (e != cudaSuccess) {
+    h0->last_error = std::string("epoch_many: ") + cudaGetErrorString(e);
+    return NOMAD_ERR_CUDA;
+  }
   return NOMAD_OK;
 }
 

@@ -72,6 +72,7 @@ SIGNATURES = {
                             ctypes.POINTER(nomad_schedule), ctypes.POINTER(_P)]),
     "nomad_load_ratings": (_I32, [_P, _I32, _I64, _P, _P, _P, _I32, _P]),
     "nomad_epoch": (_I32, [_P, _I32, _P]),
+    "nomad_epoch_many": (_I32, [ctypes.POINTER(_P), _I32, _I32, _P]),
     "nomad_check": (_I32, [_P, _P]),
     "nomad_rmse": (_I32, [_P, _I64, _P, _P, _P, _I32,
                           ctypes.POINTER(ctypes.c_double), _P]),
@@ -147,6 +148,12 @@ def nomad_load_ratings(h, fmt, nnz, major, minor, vals, device_ptrs, stream):
 
 def nomad_epoch(h, n_epochs, stream):
     _check(load_library().nomad_epoch(h, n_epochs, stream), h)
+
+
+def nomad_epoch_many(handles, n_epochs, stream):
+    arr = (_P * len(handles))(*handles)
+    _check(load_library().nomad_epoch_many(arr, len(handles), n_epochs, stream),
+           handles[0] if handles else None)
 
 
 def nomad_check(h, stream):
@@ -278,6 +285,12 @@ class Nomad:
 
     def epoch(self, n_epochs=1, stream=None):
         nomad_epoch(self.h, n_epochs, _stream_ptr(stream))
+
+    @staticmethod
+    def epoch_many(nomads, n_epochs=1, stream=None):
+        """n_epochs epochs of several independent problems in one launch
+        (nomad_epoch_many): each handle runs on its own blocks."""
+        nomad_epoch_many([nm.h for nm in nomads], n_epochs, _stream_ptr(stream))
 
     def check(self, stream=None):
         nomad_check(self.h, _stream_ptr(stream))

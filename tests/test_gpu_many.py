@@ -1,0 +1,138 @@
+"""Several independent problems in one persistent launch (nomad_epoch_many),
+against the oracle: each problem's logged visit order replays to its factors
+(binary32 and binary64, 1e-4 relative L2), its accounting is bit-exact, and
+a free run reaches the test RMSE of the same problem run alone.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1312_0193_gb300 import Nomad, NomadError  # noqa: E402
+from paper_1312_0193_gb300 import nomad as nb  # noqa: E402
+
+REPLAY_TOL = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - np.asarray(b, np.float64)) /
+                 max(np.linalg.norm(np.asarray(b, np.float64)), 1e-300))
+
+
+def make(r, k, lam, **kw):
+    nm = Nomad(r.m, r.n, k, lam, **kw)
+    nm.load_coo(r.train_rows.cuda(), r.train_cols.cuda(), r.train_vals.cuda())
+    return nm
+
+
+# (data, k, lambda, alpha, beta, workers): short and long visits, urgent items,
+# three row widths of one chunk per lane, different step-size schedules
+PROBLEMS = [
+    (lambda: synth.tiny_planted(1), 10, 0.05, 0.05, 0.05, 16),
+    (lambda: synth.netflix_shaped(0.002, seed=13), 100, 0.05, 0.01, 0.05, 24),
+    (lambda: synth.netflix_shaped(0.0005, seed=7), 64, 0.1, 0.02, 0.01, 8),
+]
+
+
+def test_many_replay_each_problem():
+    """Three problems, two calls of 3 epochs each in one launch per call;
+    every problem replays on the oracle as if it had run alone."""
+    epochs, calls = 3, 2
+    runs = []
+    try:
+        for gen, k, lam, alpha, beta, p in PROBLEMS:
+            r = gen()
+            nm = make(r, k, lam, alpha=alpha, beta=beta, debug=True, n_workers=p)
+            tr, tc, tv, *_ = r.numpy()
+            rw = oracle.partition_rows(r.m, tr, p)
+            L = oracle.build_layout(r.m, r.n, tr, tc, tv, rw, p)
+            W0, H0 = nm.factors()
+            runs.append(dict(nm=nm, L=L, lam=float(np.float32(lam)), a=float(np.float32(alpha)),
+                             b=float(np.float32(beta)), W32=W0.copy(), H32=H0.copy(),
+                             W64=W0.astype(np.float64), H64=H0.astype(np.float64),
+                             c32=None, c64=None))
+        for c in range(calls):
+            Nomad.epoch_many([x["nm"] for x in runs], epochs)
+            for x in runs:
+                nm, L = x["nm"], x["L"]
+                nm.check()
+                seg, ep = nm.replay_log()
+                S = L["seg_col"].size
+                assert seg.size == S * epochs
+                for e in range(c * epochs, (c + 1) * epochs):
+                    assert np.array_equal(np.sort(seg[ep == e]), np.arange(S))
+                x["W32"], x["H32"], x["c32"] = oracle.replay(
+                    L, seg, x["W32"], x["H32"], x["lam"], x["a"], x["b"], precision="f32",
+                    rec_count=x["c32"])
+                x["W64"], x["H64"], x["c64"] = oracle.replay(
+                    L, seg, x["W64"], x["H64"], x["lam"], x["a"], x["b"], precision="f64",
+                    rec_count=x["c64"])
+        for x in runs:
+            Wg, Hg = x["nm"].factors()
+            counts, viol = x["nm"].debug_counts()
+            assert viol == 0
+            assert np.all(counts == calls * epochs)
+            assert np.array_equal(counts, x["c32"])
+            for g, o in ((Wg, x["W32"]), (Hg, x["H32"]), (Wg, x["W64"]), (Hg, x["H64"])):
+                assert rel(g, o) < REPLAY_TOL, rel(g, o)
+    finally:
+        for x in runs:
+            x["nm"].close()
+
+
+def test_many_free_run_matches_alone():
+    """Four problems, 10 epochs in one launch: each problem's test RMSE is
+    within 0.5% of the same problem run alone with the same workers."""
+    specs = [(synth.tiny_planted(1), 10, 0.05, 16),
+             (synth.netflix_shaped(0.002, seed=13), 100, 0.05, 40),
+             (synth.netflix_shaped(0.001, seed=21), 32, 0.05, 24),
+             (synth.netflix_shaped(0.0005, seed=7), 64, 0.1, 8)]
+    alone, together = [], []
+    for r, k, lam, p in specs:
+        with make(r, k, lam, n_workers=p) as nm:
+            nm.epoch(10)
+            alone.append(nm.rmse(*r.numpy()[3:]))
+    nms = [make(r, k, lam, n_workers=p) for r, k, lam, p in specs]
+    try:
+        Nomad.epoch_many(nms, 10)
+        for nm, (r, *_rest) in zip(nms, specs):
+            nm.check()
+            together.append(nm.rmse(*r.numpy()[3:]))
+            assert nm.last_epoch_kernel_ms() > 0
+    finally:
+        for nm in nms:
+            nm.close()
+    for a, t in zip(alone, together):
+        assert abs(t - a) <= 0.005 * a, (alone, together)
+
+
+def test_many_rejects_what_it_cannot_run():
+    r = synth.tiny_planted(1)
+    a = make(r, 10, 0.05, n_workers=16)
+    b = make(r, 10, 0.05, n_workers=16, precision="bf16")
+    c = make(r, 10, 0.05, n_workers=16, mode="uniform")
+    d = Nomad(r.m, r.n, 10, 0.05)
+    big = [make(r, 10, 0.05, n_workers=800) for _ in range(2)]  # 2 x 100 blocks
+    try:
+        for hs, code in (([a, a], nb.NOMAD_ERR_INVALID_ARG),
+                         ([a, b], nb.NOMAD_ERR_UNSUPPORTED),
+                         ([a, c], nb.NOMAD_ERR_UNSUPPORTED),
+                         ([a, d], nb.NOMAD_ERR_STATE),
+                         (big, nb.NOMAD_ERR_UNSUPPORTED)):
+            with pytest.raises(NomadError) as e:
+                Nomad.epoch_many(hs, 1)
+            assert e.value.code == code, (code, e.value)
+        with pytest.raises(NomadError) as e:
+            nb.nomad_epoch_many([], 1, None)
+        assert e.value.code == nb.NOMAD_ERR_INVALID_ARG
+        # a rejected call runs nothing; a valid one still runs afterwards
+        Nomad.epoch_many([a], 2)
+        a.check()
+        assert a.info()["epochs_done"] == 2
+    finally:
+        for x in [a, b, c, d] + big:
+            x.close()
