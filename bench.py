@@ -25,6 +25,12 @@ cpu_baseline = the serial CPU oracle (binary64 shuffled SGD, one thread) on
 Several GPUs (torchrun): the path does not shard (one problem per GPU), so
 every rank runs an independent replica.  --impl reference times the CPU
 oracle instead (rank 0 only).
+
+--sweep N: N independent seeded problems of random shape, k and lambda
+(synth.sweep_specs), one epoch each per step, run as one persistent launch
+(nomad_epoch_many, blocks in proportion to each problem's ratings) and, as
+the baseline, as N launches one after another (each problem alone on every
+resident warp).
 """
 from __future__ import annotations
 
@@ -326,6 +332,141 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def sweep_blocks(nnz, total):
+    """Blocks per problem: at least one each, the rest in proportion to the
+    ratings (largest remainders)."""
+    n = len(nnz)
+    assert 0 < n <= total
+    s = float(sum(nnz))
+    want = [total * x / s for x in nnz]
+    b = [max(1, int(w)) for w in want]
+    while sum(b) > total:
+        i = max((i for i in range(n) if b[i] > 1), key=lambda i: b[i] - want[i])
+        b[i] -= 1
+    while sum(b) < total:
+        i = max(range(n), key=lambda i: want[i] - b[i])
+        b[i] += 1
+    return b
+
+
+def run_sweep(args):
+    import torch
+    import synth
+    from paper_1312_0193_gb300 import Nomad
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    specs = synth.sweep_specs(args.sweep, seed=5)
+    t0 = time.perf_counter()
+    probs = [synth.sweep_problem(sp, device=dev) for sp in specs]
+    gen_s = time.perf_counter() - t0
+    nnz = [r.nnz for r in probs]
+    total = float(sum(nnz))
+    wpb = 8
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sweep_blocks(nnz, sms)
+    alpha, beta = 0.012, 0.05
+    many, alone = [], []
+    for sp, r, b in zip(specs, probs, blocks):
+        for lst, p in ((many, b * wpb), (alone, 0)):
+            nm = Nomad(r.m, r.n, sp["k"], sp["lam"], alpha=alpha, beta=beta, device=local,
+                       n_workers=p, warps_per_block=wpb)
+            nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
+            lst.append(nm)
+    stream = torch.cuda.current_stream(dev)
+
+    def run_many():
+        Nomad.epoch_many(many, 1)
+
+    def run_alone():
+        for nm in alone:
+            nm.epoch(1)
+
+    for _ in range(args.warmup):
+        run_many()
+        run_alone()
+    torch.cuda.synchronize(dev)
+    launches0 = sum(nm.info()["kernel_launches"] for nm in many)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    kern_many = []
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            run_many()
+            kern_many.append(many[0].last_epoch_kernel_ms())
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+    launches = sum(nm.info()["kernel_launches"] for nm in many) - launches0
+    ev[2].record(stream)
+    for _ in range(args.steps):
+        run_alone()
+    ev[3].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t_many, units = reduce_max_sum(ev[0].elapsed_time(ev[1]) / 1e3, total * args.steps, world, dev)
+    t_seq, _ = reduce_max_sum(ev[2].elapsed_time(ev[3]) / 1e3, total * args.steps, world, dev)
+    # the same problems after the same epochs: test RMSE of both arms (the
+    # worker counts differ, so the visit orders and the iterates do too)
+    rm_many, rm_alone = [], []
+    for a, b, r in zip(many, alone, probs):
+        a.check()
+        b.check()
+        rm_many.append(a.rmse(r.test_rows, r.test_cols, r.test_vals))
+        rm_alone.append(b.rmse(r.test_rows, r.test_cols, r.test_vals))
+    bytes_upd = sum(n * (2 * sp["k"] * 4 + 8) for n, sp in zip(nnz, specs))
+    kern_s = statistics.mean(kern_many) / 1e3
+    peak, peak_src = load_peaks()
+    if rank == 0:
+        out = {
+            "metric": "SGD rating-updates/sec, %d independent problems per step, 1×GB300"
+                      % len(specs),
+            "value": units / t_many, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_many * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded planted problems)",
+            "config": {
+                "workload": "sweep of %d planted problems: m~U[2k,200k], n~U[1k,50k], "
+                            "density~U[0.1%%,2%%], k in {16,32,64,128}, lambda in "
+                            "{0.01,0.05,0.1,0.5}; %.3g train ratings" % (len(specs), total),
+                "alpha": alpha, "beta": beta, "step": "one epoch of every problem",
+                "blocks": blocks, "warps_per_block": wpb,
+                "l2": "inputs larger than L2 (ratings %.1f GB); no flush" % (total * 8 / 1e9),
+                "generate_seconds": round(gen_s, 1),
+                "parallelism": "replicas x%d" % world,
+            },
+            "sequential": {"value": units / t_seq, "unit": UNIT,
+                           "ms_per_step": t_seq * 1e3 / args.steps,
+                           "step": "%d nomad_epoch calls, each problem on every resident warp"
+                                   % len(specs)},
+            "speedup_vs_sequential": t_seq / t_many,
+            "test_rmse": {"epochs": args.warmup + args.steps,
+                          "one_launch_mean": statistics.mean(rm_many),
+                          "sequential_mean": statistics.mean(rm_alone),
+                          "max_rel_diff": max(abs(a - b) / b for a, b in zip(rm_many, rm_alone)),
+                          "note": "different worker counts per problem give different "
+                                  "visit orders"},
+            "roofline": {"bound": "hbm", "achieved": bytes_upd / kern_s / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": bytes_upd / kern_s / 1e9 / peak,
+                         "traffic": None, "peak_source": peak_src,
+                         "kernel": "nomad_batched_many_kernel", "kernel_ms": kern_s * 1e3},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(out), flush=True)
+    for nm in many + alone:
+        nm.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def time_to_target(args, dev, local):
     """Time to the oracle's test RMSE: the Netflix-shaped workload at
     `--ttt-scale`, generated on the CPU from its seed exactly as the oracle's
@@ -437,11 +578,15 @@ def main(argv=None):
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target leg")
     ap.add_argument("--ttt-scale", type=float, default=0.1,
                     help="workload scale of the time-to-target leg")
+    ap.add_argument("--sweep", type=int, default=0,
+                    help="time N independent problems in one launch against N launches")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep > 0:
+        run_sweep(args)
     else:
         run_ours(args)
 

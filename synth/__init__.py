@@ -20,6 +20,14 @@ in for them with their shapes and the generation recipe of Sec. 5.5):
   independently from the degree weights, duplicates dropped, more drawn until
   the target count is met); values from a planted rank-r model through a
   per-shape value map (clip/round for integer ratings).
+* planted_sparse(m, n, r, density, ...): as planted(), for shapes whose
+  m x n cells are too many to permute: uniform cell keys drawn with
+  replacement, duplicates dropped, a uniform subset of the target size kept.
+* sweep_specs(count, seed) / sweep_problem(spec): a set of independent
+  problems of random shape and hyperparameters, as for a sweep over lambda
+  and k: m ~ U[2,000, 200,000], n ~ U[1,000, 50,000], density ~ U[0.1%, 2%],
+  k in {16, 32, 64, 128}, lambda in {0.01, 0.05, 0.1, 0.5}, each a planted
+  rank-k matrix with noise 0.1 and a 1% test hold-out.
 * The train/test split is a seeded uniform hold-out restricted so that every
   test row and test column keeps at least one training rating.
 """
@@ -132,6 +140,56 @@ def planted(m: int, n: int, r: int, nnz_total: int, noise: float,
     n_test = int(round(test_frac * nnz_total))
     parts = _split(rows, cols, vals.float(), n_test, m, n, g)
     return Ratings(m, n, *parts, name=name)
+
+
+def planted_sparse(m: int, n: int, r: int, density: float, noise: float,
+                   test_frac: float, seed: int, device="cpu", name="planted-sparse") -> Ratings:
+    """Uniformly observed planted low-rank matrix with about density*m*n
+    entries, drawn without permuting all m*n cells."""
+    g = _gen(seed, device)
+    target = max(1, int(round(density * m * n)))
+    cells = m * n
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    for _ in range(64):
+        need = target - keys.numel()
+        if need <= 0:
+            break
+        draw = torch.randint(0, cells, (int(need * 1.1) + 16,), generator=g, device=device)
+        keys = torch.unique(torch.cat([keys, draw]))
+    keys = keys[torch.randperm(keys.numel(), generator=g, device=device)[:target]]
+    rows = (keys // n).to(torch.int32)
+    cols = (keys % n).to(torch.int32)
+    std = (1.0 / math.sqrt(r)) ** 0.5
+    U = torch.randn(m, r, generator=g, device=device) * std
+    V = torch.randn(n, r, generator=g, device=device) * std
+    vals = _truth_dot(rows, cols, U, V)
+    if noise > 0:
+        vals = vals + noise * torch.randn(vals.shape, generator=g, device=device)
+    rows, cols, vals = _sort_rowmajor(rows, cols, vals, n)
+    n_test = int(round(test_frac * rows.numel()))
+    parts = _split(rows, cols, vals.float(), n_test, m, n, g)
+    return Ratings(m, n, *parts, name=name)
+
+
+def sweep_specs(count: int = 64, seed: int = 5) -> list:
+    """Shapes and hyperparameters of `count` independent problems (see the
+    module docstring); problem i is generated from seed 1000 * seed + i."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        out.append(dict(m=int(rng.integers(2000, 200001)), n=int(rng.integers(1000, 50001)),
+                        density=float(rng.uniform(0.001, 0.02)),
+                        k=int(rng.choice([16, 32, 64, 128])),
+                        lam=float(rng.choice([0.01, 0.05, 0.1, 0.5])),
+                        seed=1000 * seed + i))
+    return out
+
+
+def sweep_problem(spec: dict, device="cpu") -> Ratings:
+    return planted_sparse(spec["m"], spec["n"], spec["k"], spec["density"], 0.1, 0.01,
+                          spec["seed"], device,
+                          name="sweep-%d m=%d n=%d k=%d" % (spec["seed"] % 1000, spec["m"],
+                                                           spec["n"], spec["k"]))
 
 
 def tiny_planted(seed: int = 1, device="cpu") -> Ratings:

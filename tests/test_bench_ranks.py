@@ -8,6 +8,7 @@ runs the reference arm, are exercised here without a GPU.
 import os
 import socket
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -62,3 +63,38 @@ def test_reference_arm_other_ranks_do_nothing(capsys, monkeypatch):
     monkeypatch.setenv("LOCAL_RANK", "1")
     bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"])
     assert capsys.readouterr().out == ""
+
+
+def test_sweep_block_allocation():
+    """Blocks of the several-problem launch: every problem at least one, all
+    blocks used, the rest in proportion to the ratings."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    import synth
+    assert bench.sweep_blocks([5, 1, 1], 3) == [1, 1, 1]
+    assert bench.sweep_blocks([100, 1], 152) == [150, 2]
+    assert bench.sweep_blocks([1, 1, 1, 1], 8) == [2, 2, 2, 2]
+    specs = synth.sweep_specs(64, seed=5)
+    assert specs == synth.sweep_specs(64, seed=5)  # seeded
+    nnz = [int(s["m"] * s["n"] * s["density"]) for s in specs]
+    b = bench.sweep_blocks(nnz, 152)
+    assert sum(b) == 152 and min(b) >= 1
+    share = [x / sum(nnz) * 152 for x in nnz]
+    assert all(abs(bi - si) < 1.0 or bi == 1 for bi, si in zip(b, share))
+    for s in specs:
+        assert 2000 <= s["m"] <= 200000 and 1000 <= s["n"] <= 50000
+        assert 0.001 <= s["density"] <= 0.02
+        assert s["k"] in (16, 32, 64, 128) and s["lam"] in (0.01, 0.05, 0.1, 0.5)
+
+
+def test_planted_sparse_is_a_set_with_its_density():
+    import synth
+    r = synth.planted_sparse(3000, 1500, 16, 0.01, 0.1, 0.01, seed=9)
+    tr, tc, tv, er, ec, ev = r.numpy()
+    rows = np.concatenate([tr, er]).astype(np.int64)
+    cols = np.concatenate([tc, ec]).astype(np.int64)
+    keys = rows * 1500 + cols
+    assert np.unique(keys).size == keys.size  # Omega is a set
+    assert keys.size == round(0.01 * 3000 * 1500)
+    assert rows.min() >= 0 and rows.max() < 3000 and cols.min() >= 0 and cols.max() < 1500
