@@ -28,7 +28,8 @@ oracle instead (rank 0 only).
 
 --sweep N: N independent seeded problems of random shape, k and lambda
 (synth.sweep_specs), one epoch each per step, run as one persistent launch
-(nomad_epoch_many, blocks in proportion to each problem's ratings) and, as
+(nomad_epoch_many; blocks in proportion to each problem's ratings, then
+re-allocated from each problem's measured device time span) and, as
 the baseline, as N launches one after another (each problem alone on every
 resident warp).
 """
@@ -368,15 +369,46 @@ def run_sweep(args):
     total = float(sum(nnz))
     wpb = 8
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    blocks = sweep_blocks(nnz, sms)
     alpha, beta = 0.012, 0.05
-    many, alone = [], []
-    for sp, r, b in zip(specs, probs, blocks):
-        for lst, p in ((many, b * wpb), (alone, 0)):
+
+    def handles(workers):
+        out = []
+        for sp, r, p in zip(specs, probs, workers):
             nm = Nomad(r.m, r.n, sp["k"], sp["lam"], alpha=alpha, beta=beta, device=local,
                        n_workers=p, warps_per_block=wpb)
             nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
-            lst.append(nm)
+            out.append(nm)
+        return out
+
+    # blocks in proportion to the ratings, then --sweep-tune rounds of: one
+    # epoch in one launch, each problem's device time span read back, blocks
+    # in proportion to each problem's block-seconds (span x blocks); the
+    # allocation measured fastest is kept (a problem's span does not fall in
+    # proportion to its blocks: more workers also lengthen each item's chain
+    # of visits)
+    blocks = sweep_blocks(nnz, sms)
+    tuning = []
+    best = None
+    for _ in range(args.sweep_tune):
+        cal = handles([b * wpb for b in blocks])
+        Nomad.epoch_many(cal, 1)
+        ms = cal[0].last_epoch_kernel_ms()
+        spans = [nm.last_epoch_span_ns() for nm in cal]
+        for nm in cal:
+            nm.close()
+        tuning.append({"blocks": blocks, "kernel_ms": round(ms, 2),
+                       "slowest_span_ms": round(max(spans) / 1e6, 2),
+                       "mean_span_ms": round(statistics.mean(spans) / 1e6, 2)})
+        if best is None or ms < best[0]:
+            best = (ms, blocks)
+        new = sweep_blocks([max(sp, 1) * b for sp, b in zip(spans, blocks)], sms)
+        if new == blocks:
+            break
+        blocks = new
+    if best is not None:
+        blocks = best[1]
+    many = handles([b * wpb for b in blocks])
+    alone = handles([0] * len(specs))
     stream = torch.cuda.current_stream(dev)
 
     def run_many():
@@ -436,7 +468,7 @@ def run_sweep(args):
                             "density~U[0.1%%,2%%], k in {16,32,64,128}, lambda in "
                             "{0.01,0.05,0.1,0.5}; %.3g train ratings" % (len(specs), total),
                 "alpha": alpha, "beta": beta, "step": "one epoch of every problem",
-                "blocks": blocks, "warps_per_block": wpb,
+                "blocks": blocks, "warps_per_block": wpb, "tuning": tuning,
                 "l2": "inputs larger than L2 (ratings %.1f GB); no flush" % (total * 8 / 1e9),
                 "generate_seconds": round(gen_s, 1),
                 "parallelism": "replicas x%d" % world,
@@ -580,6 +612,8 @@ def main(argv=None):
                     help="workload scale of the time-to-target leg")
     ap.add_argument("--sweep", type=int, default=0,
                     help="time N independent problems in one launch against N launches")
+    ap.add_argument("--sweep-tune", type=int, default=2,
+                    help="rounds of block re-allocation from measured per-problem spans")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

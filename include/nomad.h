@@ -189,6 +189,15 @@ NOMAD_API int nomad_epoch(nomad_t *h, int32_t n_epochs, void *stream);
 NOMAD_API int nomad_epoch_many(nomad_t *const *h, int32_t count, int32_t n_epochs,
                                void *stream);
 
+/* Device time span, in nanoseconds, of the handle's workers in its last
+ * nomad_epoch / nomad_epoch_many call with the batched variant: from the
+ * first worker's start to the last worker's end (the device's global
+ * timer).  In a nomad_epoch_many launch this is the handle's own problem,
+ * which is how a caller sees which problem the launch waited for.  Waits for
+ * the handle's work on `stream`.  *ns = 0 when no such call has run (or the
+ * simple variant or uniform mode ran). */
+NOMAD_API int nomad_last_epoch_span_ns(nomad_t *h, int64_t *ns, void *stream);
+
 /* Wait for the handle's work on `stream` and report any device-side error
  * of earlier nomad_epoch calls (then clears it). */
 NOMAD_API int nomad_check(nomad_t *h, void *stream);

@@ -436,6 +436,7 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
   int4* meta_b = meta_a + kBatch;                          // {beg_lo, beg_hi, lane, soff}
 
   const int64_t quota = int64_t(P.worker_seg_ptr[q + 1] - P.worker_seg_ptr[q]) * P.n_epochs;
+  if (lane == 0) atomicMin(P.span, globaltimer_ns());  // the launch's time span on the device
   const int lg = P.ring_log2[q];
   const uint32_t qmask = (1u << lg) - 1u;
   const unsigned long long* ring_q = P.ring + P.ring_base[q];
@@ -874,6 +875,7 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
     __syncwarp();  // orders every lane's H stores before the releases below
     if (late && nseg >= 0) push_token(P, q2, uint32_t(j));
   }
+  if (lane == 0) atomicMax(P.span + 1, globaltimer_ns());
 }
 
 template <int CPL, bool BF, bool DEBUG>

@@ -239,6 +239,9 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
   h->result = static_cast<double*>(vp);
   if (dev_alloc(h, &vp, sizeof(unsigned long long) * 2) != cudaSuccess) goto oom;
   h->upd_done = static_cast<unsigned long long*>(vp);
+  if (dev_alloc(h, &vp, sizeof(unsigned long long) * 2) != cudaSuccess) goto oom;
+  h->span = static_cast<unsigned long long*>(vp);
+  if (cudaMemset(h->span, 0, sizeof(unsigned long long) * 2) != cudaSuccess) goto cuda_err;
   if (dev_alloc(h, &vp, sizeof(int32_t) * 2) != cudaSuccess) goto oom;
   h->stop = static_cast<int32_t*>(vp);
   if (dev_alloc(h, &vp, sizeof(uint32_t) * 2) != cudaSuccess) goto oom;
@@ -419,6 +422,18 @@ int nomad_epoch_many(nomad_t* const* hs, int32_t count, int32_t n_epochs, void* 
   const int rc = launch_epochs_many(hs, count, n_epochs, st);
   if (rc != NOMAD_OK) return rc;
   for (int g = 0; g < count; ++g) hs[g]->epochs_done += n_epochs;
+  return NOMAD_OK;
+}
+
+int nomad_last_epoch_span_ns(nomad_t* h, int64_t* ns, void* stream) {
+  if (!h || !ns) return NOMAD_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  cudaStream_t st = as_stream(stream);
+  unsigned long long span[2] = {0, 0};
+  CK(h, cudaMemcpyAsync(span, h->span, sizeof(span), cudaMemcpyDeviceToHost, st),
+     "last_epoch_span_ns");
+  CK(h, cudaStreamSynchronize(st), "last_epoch_span_ns");
+  *ns = span[1] > span[0] ? int64_t(span[1] - span[0]) : 0;
   return NOMAD_OK;
 }
 

@@ -138,6 +138,7 @@ struct SgdParams {
   uint32_t seed_lo, seed_hi;
   int64_t timeout_ns;
   int32_t* status;
+  unsigned long long* span;  // 2 words: first worker start, last worker end (globaltimer ns)
   // uniform mode
   unsigned long long* upd_done;
   unsigned long long upd_budget;
@@ -212,6 +213,7 @@ struct nomad_handle {
   float* step = nullptr;
   int32_t step_cap = 0;
   int32_t* status = nullptr;       // kStatusWords
+  unsigned long long* span = nullptr;  // device time span of the last batched launch
   unsigned long long* upd_done = nullptr;
   int32_t* stop = nullptr;
   // scratch for reductions

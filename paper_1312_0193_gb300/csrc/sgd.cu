@@ -455,6 +455,7 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
   P.seed_hi = uint32_t(h->sched.seed >> 32);
   P.timeout_ns = h->sched.spin_timeout_ns > 0 ? h->sched.spin_timeout_ns : 10000000000ll;
   P.status = h->status;
+  P.span = h->span;
   P.upd_done = uniform ? h->upd_done : nullptr;
   P.upd_budget = static_cast<unsigned long long>(n_epochs) * static_cast<unsigned long long>(h->nnz);
   P.stop = uniform ? h->stop : nullptr;
@@ -474,7 +475,9 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
                                         sizeof(unsigned long long) * (int64_t(h->p) << h->uring_log2),
                                         st))) ||
       (h->uring_tail && (e = cudaMemsetAsync(h->uring_tail, 0, sizeof(uint32_t) * h->p, st))) ||
-      (e = cudaMemsetAsync(h->status, 0, sizeof(int32_t) * kStatusWords, st))) {
+      (e = cudaMemsetAsync(h->status, 0, sizeof(int32_t) * kStatusWords, st)) ||
+      (e = cudaMemsetAsync(h->span, 0xff, sizeof(unsigned long long), st)) ||
+      (e = cudaMemsetAsync(h->span + 1, 0, sizeof(unsigned long long), st))) {
     h->last_error = std::string("epoch: ") + cudaGetErrorString(e);
     return NOMAD_ERR_CUDA;
   }

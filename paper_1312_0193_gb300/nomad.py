@@ -73,6 +73,7 @@ SIGNATURES = {
     "nomad_load_ratings": (_I32, [_P, _I32, _I64, _P, _P, _P, _I32, _P]),
     "nomad_epoch": (_I32, [_P, _I32, _P]),
     "nomad_epoch_many": (_I32, [ctypes.POINTER(_P), _I32, _I32, _P]),
+    "nomad_last_epoch_span_ns": (_I32, [_P, ctypes.POINTER(ctypes.c_int64), _P]),
     "nomad_check": (_I32, [_P, _P]),
     "nomad_rmse": (_I32, [_P, _I64, _P, _P, _P, _I32,
                           ctypes.POINTER(ctypes.c_double), _P]),
@@ -326,6 +327,14 @@ class Nomad:
         if dw != dh:
             raise ValueError("W and H must both be on the GPU or both on the host")
         nomad_set_factors(self.h, w, h, dw, epochs_done, _stream_ptr(stream))
+
+    def last_epoch_span_ns(self, stream=None) -> int:
+        """Device time of this handle's workers in the last batched epoch
+        call (first start to last end), in nanoseconds."""
+        ns = ctypes.c_int64(0)
+        _check(load_library().nomad_last_epoch_span_ns(self.h, ctypes.byref(ns),
+                                                       _stream_ptr(stream)), self.h)
+        return int(ns.value)
 
     def last_epoch_kernel_ms(self) -> float:
         """Device time of the last persistent kernel (CUDA events)."""

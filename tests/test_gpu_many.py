@@ -99,10 +99,17 @@ def test_many_free_run_matches_alone():
     nms = [make(r, k, lam, n_workers=p) for r, k, lam, p in specs]
     try:
         Nomad.epoch_many(nms, 10)
+        ms = nms[0].last_epoch_kernel_ms()
+        spans = [nm.last_epoch_span_ns() for nm in nms]
+        # each problem's device span lies within the launch (CUDA events),
+        # and the launch lasts about as long as its slowest problem
+        assert all(0 < s <= ms * 1e6 * 1.02 + 5e4 for s in spans), (spans, ms)
+        assert max(spans) >= 0.5 * ms * 1e6, (spans, ms)
         for nm, (r, *_rest) in zip(nms, specs):
             nm.check()
             together.append(nm.rmse(*r.numpy()[3:]))
-            assert nm.last_epoch_kernel_ms() > 0
+            # every handle records its own events around the one launch
+            assert abs(nm.last_epoch_kernel_ms() - ms) < 0.05
     finally:
         for nm in nms:
             nm.close()
