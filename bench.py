@@ -159,7 +159,17 @@ def make_workload(cfg: str, device, scale: float = 1.0):
     gen, k, lam, alpha, beta = CONFIGS[cfg]
     fn = getattr(synth, gen)
     r = fn(device=device) if cfg == "tiny" else fn(scale, device=device)
+    release_cache(device)
     return r, k, lam, alpha, beta
+
+
+def release_cache(device):
+    """Hand the generator's freed device memory back to the driver: the
+    library allocates with the CUDA runtime, not through torch's cache."""
+    import torch
+    if torch.device(device).type == "cuda":
+        torch.cuda.synchronize(device)
+        torch.cuda.empty_cache()
 
 
 def workload_name(r, k):
@@ -305,7 +315,8 @@ def run_ours(args):
                 "ratings_per_visit": round(nnz / max(info["n_segments"], 1), 3),
                 "step": "one epoch (all ratings) + test RMSE",
                 "l2": "inputs larger than L2 (ratings %.0f MB, W %.0f MB); no flush" % (
-                    nnz * 8 / 1e6, r.m * info["pitch"] * 4 / 1e6),
+                    nnz * 8 / 1e6,
+                    r.m * info["pitch"] * (2 if args.precision == "bf16" else 4) / 1e6),
                 "parallelism": "replicas x%d (one independent problem per GPU)" % world,
                 "load_seconds_first": round(load_s, 3),
             },
@@ -364,6 +375,7 @@ def run_sweep(args):
     specs = synth.sweep_specs(args.sweep, seed=5)
     t0 = time.perf_counter()
     probs = [synth.sweep_problem(sp, device=dev) for sp in specs]
+    release_cache(dev)
     gen_s = time.perf_counter() - t0
     nnz = [r.nnz for r in probs]
     total = float(sum(nnz))

@@ -98,22 +98,53 @@ def _truth_dot(rows, cols, U, V, chunk=1 << 22):
     return out
 
 
+# Above this many elements the generators work in chunks: torch's unique,
+# randperm and boolean indexing go through CUB, which takes fewer than 2^31.
+_CHUNK = 1 << 30
+
+
+def _masked(x, mask):
+    """x[mask], chunk by chunk for long tensors."""
+    if x.numel() <= _CHUNK:
+        return x[mask]
+    return torch.cat([x[s:s + _CHUNK][mask[s:s + _CHUNK]]
+                      for s in range(0, x.numel(), _CHUNK)])
+
+
+def _bincount(x, minlength):
+    if x.numel() <= _CHUNK:
+        return torch.bincount(x.long(), minlength=minlength)
+    out = torch.zeros(minlength, dtype=torch.int64, device=x.device)
+    for s in range(0, x.numel(), _CHUNK):
+        out += torch.bincount(x[s:s + _CHUNK].long(), minlength=minlength)
+    return out
+
+
 def _split(rows, cols, vals, n_test, m, n, g):
     """Uniform hold-out of about n_test entries; a test entry whose row or
     column would be left without a training entry goes back to training."""
     nnz = rows.numel()
     dev = rows.device
-    perm = torch.randperm(nnz, generator=g, device=dev)
     is_test = torch.zeros(nnz, dtype=torch.bool, device=dev)
-    is_test[perm[:n_test]] = True
+    if nnz <= _CHUNK:
+        perm = torch.randperm(nnz, generator=g, device=dev)
+        is_test[perm[:n_test]] = True
+    else:  # n_test distinct positions drawn uniformly
+        pick = torch.empty(0, dtype=torch.int64, device=dev)
+        while pick.numel() < n_test:
+            draw = torch.randint(0, nnz, (int((n_test - pick.numel()) * 1.1) + 16,),
+                                 generator=g, device=dev)
+            pick = torch.unique(torch.cat([pick, draw]))
+        pick = pick[torch.randperm(pick.numel(), generator=g, device=dev)[:n_test]]
+        is_test[pick] = True
     tr = ~is_test
-    rdeg = torch.bincount(rows[tr].long(), minlength=m)
-    cdeg = torch.bincount(cols[tr].long(), minlength=n)
+    rdeg = _bincount(_masked(rows, tr), m)
+    cdeg = _bincount(_masked(cols, tr), n)
     bad = is_test & ((rdeg[rows.long()] == 0) | (cdeg[cols.long()] == 0))
     is_test &= ~bad
     tr = ~is_test
-    return (rows[tr], cols[tr], vals[tr], rows[is_test], cols[is_test],
-            vals[is_test])
+    return (_masked(rows, tr), _masked(cols, tr), _masked(vals, tr), _masked(rows, is_test),
+            _masked(cols, is_test), _masked(vals, is_test))
 
 
 def _sort_rowmajor(rows, cols, vals, n):
@@ -225,6 +256,8 @@ def zipf_degrees(count: int, total: float, s: float, cap: float, g) -> torch.Ten
 
 def _sample_pairs(du, dv, target, n, g, max_rounds=64):
     """Distinct (i, j) pairs, i ~ du / sum(du), j ~ dv / sum(dv)."""
+    if target > _CHUNK:
+        return _sample_pairs_chunked(du, dv, target, n, g, max_rounds)
     dev = du.device
     cu = torch.cumsum(du, 0)
     cu = cu / cu[-1]
@@ -247,6 +280,52 @@ def _sample_pairs(du, dv, target, n, g, max_rounds=64):
         pick = torch.randperm(keys.numel(), generator=g, device=dev)[:target]
         keys = torch.sort(keys[pick]).values
     return keys
+
+
+def _sample_pairs_chunked(du, dv, target, n, g, max_rounds=64):
+    """_sample_pairs for more than _CHUNK pairs: the users are cut into
+    ranges of about equal degree weight, each range receives its share of the
+    pairs (i drawn from the range's weights, j from all items), and pairs are
+    made distinct within a range (ranges share no user)."""
+    dev = du.device
+    cu = torch.cumsum(du.double(), 0)
+    total_w = float(cu[-1])
+    nchunks = (target + _CHUNK // 2 - 1) // (_CHUNK // 2)
+    # user boundaries at equal weight fractions
+    cuts = torch.searchsorted(cu, torch.linspace(0, total_w, nchunks + 1, device=dev,
+                                                 dtype=torch.float64)[1:-1])
+    bounds = [0] + [int(c) + 1 for c in cuts.tolist()] + [du.numel()]
+    cv = torch.cumsum(dv.double(), 0)
+    cv = cv / cv[-1]
+    out, assigned = [], 0
+    for c in range(nchunks):
+        lo, hi = bounds[c], bounds[c + 1]
+        if hi <= lo:
+            continue
+        w_lo = float(cu[lo - 1]) if lo > 0 else 0.0
+        w_hi = float(cu[hi - 1])
+        t_c = target - assigned if c == nchunks - 1 else int(round(target * (w_hi - w_lo) / total_w))
+        t_c = min(t_c, (hi - lo) * int(dv.numel()))
+        assigned += t_c
+        cuc = (cu[lo:hi] - w_lo) / (w_hi - w_lo)
+        keys = torch.empty(0, dtype=torch.int64, device=dev)
+        for _ in range(max_rounds):
+            need = t_c - keys.numel()
+            if need <= 0:
+                break
+            draw = int(need * 1.15) + 1024
+            i = torch.searchsorted(cuc, torch.rand(draw, generator=g, device=dev,
+                                                   dtype=torch.float64))
+            j = torch.searchsorted(cv, torch.rand(draw, generator=g, device=dev,
+                                                  dtype=torch.float64))
+            i = i.clamp_(max=hi - lo - 1) + lo
+            j = j.clamp_(max=dv.numel() - 1)
+            keys = torch.unique(torch.cat([keys, i * n + j]))
+        if keys.numel() > t_c:
+            pick = torch.randperm(keys.numel(), generator=g, device=dev)[:t_c]
+            keys = torch.sort(keys[pick]).values
+        out.append(keys)
+    return torch.cat(out)
 
 
 def skewed(m: int, n: int, nnz_train: int, nnz_test: int, user_s: float,

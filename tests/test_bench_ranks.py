@@ -8,7 +8,6 @@ runs the reference arm, are exercised here without a GPU.
 import os
 import socket
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -87,14 +86,3 @@ def test_sweep_block_allocation():
         assert 0.001 <= s["density"] <= 0.02
         assert s["k"] in (16, 32, 64, 128) and s["lam"] in (0.01, 0.05, 0.1, 0.5)
 
-
-def test_planted_sparse_is_a_set_with_its_density():
-    import synth
-    r = synth.planted_sparse(3000, 1500, 16, 0.01, 0.1, 0.01, seed=9)
-    tr, tc, tv, er, ec, ev = r.numpy()
-    rows = np.concatenate([tr, er]).astype(np.int64)
-    cols = np.concatenate([tc, ec]).astype(np.int64)
-    keys = rows * 1500 + cols
-    assert np.unique(keys).size == keys.size  # Omega is a set
-    assert keys.size == round(0.01 * 3000 * 1500)
-    assert rows.min() >= 0 and rows.max() < 3000 and cols.min() >= 0 and cols.max() < 1500
