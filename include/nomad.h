@@ -50,7 +50,7 @@ extern "C" {
 #define NOMAD_ERR_OWNERSHIP (-5)   /* debug check: an item token held by two workers */
 #define NOMAD_ERR_CUDA (-6)        /* a CUDA runtime call failed */
 #define NOMAD_ERR_RANGE (-7)       /* an index is outside [0,m) or [0,n) */
-#define NOMAD_ERR_UNSUPPORTED (-8) /* shape or option this build does not handle */
+#define NOMAD_ERR_UNSUPPORTED (-8) /* shape or option the library does not handle */
 #define NOMAD_ERR_STATE (-9)       /* e.g. nomad_epoch before nomad_load_ratings */
 
 /* ---------------------------------------------------------------- options */
