@@ -68,6 +68,17 @@ def _lib():
         lib.orc_replay_bf16.argtypes = [i32, f32, f64, f64, i64, P, P, i64, P, P,
                                         P, P, P, P, P, u64]
         lib.orc_replay_bf16.restype = i32
+        lib.orc_e4m3_rn_n.argtypes = [i64, P, P]
+        lib.orc_e4m3_rn_n.restype = None
+        lib.orc_e4m3_sr_n.argtypes = [i64, P, P, P]
+        lib.orc_e4m3_sr_n.restype = None
+        lib.orc_e4m3_to_f32_n.argtypes = [i64, P, P]
+        lib.orc_e4m3_to_f32_n.restype = None
+        lib.orc_e4m3_rows.argtypes = [i64, i32, P, P, P, P]
+        lib.orc_e4m3_rows.restype = None
+        lib.orc_replay_e4m3.argtypes = [i32, f32, f64, f64, i64, P, P, i64, P, P,
+                                        P, P, P, P, P, P, u64]
+        lib.orc_replay_e4m3.restype = i32
         _LIB = lib
     return _LIB
 
@@ -353,3 +364,78 @@ def replay_bf16(layout: dict, visit_seg, visit_epoch, Wb, Hb, lam: float,
     if rc != 0:
         raise ValueError("replay_bf16: bad segment index or allocation failure")
     return Wb, Hb, cnt
+
+
+# ---------------------------------------------------------------- FP8 E4M3
+def e4m3_rn(x) -> np.ndarray:
+    """E4M3 codes (uint8) of binary32 values, round to nearest even,
+    saturating at 448."""
+    x = _c(x, np.float32)
+    out = np.zeros(x.shape, dtype=np.uint8)
+    _lib().orc_e4m3_rn_n(x.size, _ptr(x), _ptr(out))
+    return out
+
+
+def e4m3_sr(x, r16) -> np.ndarray:
+    """Stochastic rounding of binary32 values to E4M3 with the given 16
+    random bits per value (see the C source for the rule)."""
+    x = _c(x, np.float32)
+    r = _c(r16, np.uint32)
+    assert r.shape == x.shape
+    out = np.zeros(x.shape, dtype=np.uint8)
+    _lib().orc_e4m3_sr_n(x.size, _ptr(x), _ptr(r), _ptr(out))
+    return out
+
+
+def e4m3_to_f32(c) -> np.ndarray:
+    c = _c(c, np.uint8)
+    out = np.zeros(c.shape, dtype=np.float32)
+    _lib().orc_e4m3_to_f32_n(c.size, _ptr(c), _ptr(out))
+    return out
+
+
+def e4m3_rows(W, r16=None):
+    """Per-row scaled E4M3 storage of the rows of W (binary32, rows x k):
+    (codes uint8 rows x k, scales float32 rows); r16 = None rounds to
+    nearest, else stochastic with r16 (uint32, rows x k)."""
+    W = _c(W, np.float32)
+    rows, k = W.shape
+    codes = np.zeros((rows, k), dtype=np.uint8)
+    scales = np.zeros(rows, dtype=np.float32)
+    r = None if r16 is None else _c(r16, np.uint32)
+    if r is not None:
+        assert r.shape == W.shape
+    _lib().orc_e4m3_rows(rows, k, _ptr(W), None if r is None else _ptr(r), _ptr(codes),
+                         _ptr(scales))
+    return codes, scales
+
+
+def e4m3_decode_rows(codes, scales) -> np.ndarray:
+    """The stored binary32 values: scale * decode(code), row by row."""
+    return (e4m3_to_f32(codes) * _c(scales, np.float32)[:, None]).astype(np.float32)
+
+
+def replay_e4m3(layout: dict, visit_seg, visit_epoch, Wc, Ws, H, lam: float,
+                alpha: float, beta: float, seed: int, rec_count=None):
+    """Replay with W stored as per-row scaled E4M3 (codes Wc m x k, scales Ws
+    m) and H in binary32 (see the C source).  Returns (Wc, Ws, H,
+    rec_count)."""
+    visit_seg = _c(visit_seg, np.int64)
+    visit_epoch = _c(visit_epoch, np.int32)
+    assert visit_seg.shape == visit_epoch.shape
+    Wc = _c(Wc, np.uint8).copy()
+    Ws = _c(Ws, np.float32).copy()
+    H = _c(H, np.float32).copy()
+    seg_col = _c(layout["seg_col"], np.int32)
+    rec_row = _c(layout["rec_row"], np.int32)
+    rec_val = _c(layout["rec_val"], np.float32)
+    cnt = (np.zeros(rec_row.size, dtype=np.int32) if rec_count is None
+           else _c(rec_count, np.int32).copy())
+    rc = _lib().orc_replay_e4m3(Wc.shape[1], lam, alpha, beta, visit_seg.size,
+                                _ptr(visit_seg), _ptr(visit_epoch), seg_col.size,
+                                _ptr(layout["seg_ptr"]), _ptr(seg_col), _ptr(rec_row),
+                                _ptr(rec_val), _ptr(Wc), _ptr(Ws), _ptr(H), _ptr(cnt),
+                                seed)
+    if rc != 0:
+        raise ValueError("replay_e4m3: bad segment index or allocation failure")
+    return Wc, Ws, H, cnt

@@ -527,3 +527,141 @@ void orc_bf16_sr_n(int64_t n, const float *x, const uint32_t *r16, uint16_t *out
 void orc_bf16_to_f32_n(int64_t n, const uint16_t *b, float *out) {
   for (int64_t i = 0; i < n; ++i) out[i] = orc_bf16_to_f32(b[i]);
 }
+
+/* ------------------------------------------------------------------------ */
+/* FP8-E4M3 storage of W with one binary32 scale per row (a storage variant */
+/* like the bfloat16 one; H stays binary32).                                */
+/*                                                                          */
+/* E4M3: sign, 4 exponent bits (bias 7), 3 mantissa bits.  Exponent field 0 */
+/* holds the subnormals m * 2^-9 (m = 0..7); otherwise the value is         */
+/* (1 + m/8) * 2^(E-7).  The largest finite magnitude is 448 (E=15, m=6);   */
+/* E=15, m=7 is NaN; there is no infinity.                                  */
+/*                                                                          */
+/* Rounding of a binary32 x to E4M3 (sign kept, magnitude |x| rounded):    */
+/*  - |x| >= 2^-6 (normal range): keep 3 of the 23 mantissa bits.  Nearest */
+/*    (ties to even): add 0x7ffff plus the lowest kept bit, truncate.       */
+/*    Stochastic with 16 random bits r: add r << 4 to the 20 dropped bits,   */
+/*    truncate; the magnitude rounds up with probability (dropped bits      */
+/*    >> 4) / 2^16.                                                          */
+/*  - |x| < 2^-6: the grid is m * 2^-9.  With t = |x| * 2^9 and             */
+/*    f = t - floor(t) (both exact in binary32): nearest rounds up when      */
+/*    f > 1/2, or f = 1/2 with floor(t) odd; stochastic rounds up when        */
+/*    r < f * 2^16.  m = 8 is the smallest normal, code 0x08.               */
+/*  - Magnitudes above 448 after rounding, and infinities, become 448; NaN  */
+/*    becomes the NaN code.                                                  */
+/*                                                                          */
+/* A row w (k binary32 entries) is stored as codes c_l and a scale s:      */
+/*   a = max_l |w_l|; if a >= 2^-100: s = a / 448, g = 448 / a (binary32    */
+/*   divisions), else s = 1, g = 1; c_l = round(w_l * g) (binary32 product). */
+/* Its stored value is s * decode(c_l) (binary32 product).                  */
+/* ------------------------------------------------------------------------ */
+static uint8_t e4m3_from_rounded(uint32_t sign, uint32_t u) {
+  /* u: a binary32 magnitude with at most 3 mantissa bits, >= 2^-6 */
+  const int32_t e = (int32_t)((u >> 23) & 0xffu) - 127;
+  if (e > 8 || (e == 8 && ((u >> 20) & 7u) == 7u)) return (uint8_t)(sign | 0x7eu);
+  return (uint8_t)(sign | ((uint32_t)(e + 7) << 3) | ((u >> 20) & 7u));
+}
+
+static uint8_t e4m3_round(float x, int stochastic, uint32_t r16) {
+  const uint32_t bits = f32_bits(x);
+  const uint32_t sign = (bits >> 24) & 0x80u;
+  uint32_t u = bits & 0x7fffffffu;
+  if (u > 0x7f800000u) return (uint8_t)(sign | 0x7fu);  /* NaN */
+  if (u == 0x7f800000u) return (uint8_t)(sign | 0x7eu); /* infinity saturates */
+  if (u >= 0x3c800000u) {                                /* |x| >= 2^-6 */
+    if (stochastic) u += (r16 & 0xffffu) << 4;
+    else u += 0x7ffffu + ((u >> 20) & 1u);
+    u &= ~0xfffffu;
+    return e4m3_from_rounded(sign, u);
+  }
+  const float t = bits_f32(u) * 512.0f;
+  const float lo = floorf(t);
+  const float f = t - lo;
+  uint32_t m = (uint32_t)lo;
+  int up;
+  if (stochastic) up = (float)(r16 & 0xffffu) < f * 65536.0f;
+  else up = f > 0.5f || (f == 0.5f && (m & 1u));
+  if (up) m += 1u;
+  return (uint8_t)(sign | m); /* m <= 8: code m (8 is the smallest normal) */
+}
+
+uint8_t orc_e4m3_rn(float x) { return e4m3_round(x, 0, 0u); }
+uint8_t orc_e4m3_sr(float x, uint32_t r16) { return e4m3_round(x, 1, r16); }
+
+float orc_e4m3_to_f32(uint8_t c) {
+  const uint32_t e = (c >> 3) & 15u, m = c & 7u;
+  float v;
+  if (e == 15u && m == 7u) v = NAN;
+  else if (e == 0u) v = ldexpf((float)m, -9);
+  else v = ldexpf(1.0f + (float)m / 8.0f, (int)e - 7);
+  return (c & 0x80u) ? -v : v;
+}
+
+/* Codes and scale of a row (r16 = NULL: round to nearest). */
+void orc_e4m3_row(int32_t k, const float *w, const uint32_t *r16, uint8_t *codes,
+                  float *scale) {
+  float a = 0.0f;
+  for (int32_t l = 0; l < k; ++l) a = fmaxf(a, fabsf(w[l]));
+  float s = 1.0f, g = 1.0f;
+  if (a >= 0x1p-100f) {
+    s = a / 448.0f;
+    g = 448.0f / a;
+  }
+  for (int32_t l = 0; l < k; ++l)
+    codes[l] = r16 ? orc_e4m3_sr(w[l] * g, r16[l]) : orc_e4m3_rn(w[l] * g);
+  *scale = s;
+}
+
+/* Replay with W in E4M3 codes plus a binary32 scale per row and H in
+ * binary32: per rating, w_i is decoded (scale * value), the update of
+ * orc_sgd_update_f32 is applied, and w_i is re-encoded with stochastic
+ * rounding (the 16 random bits of entry l as for the bfloat16 W); h_j is
+ * updated in place in binary32. */
+int32_t orc_replay_e4m3(int32_t k, float lambda, double alpha, double beta,
+                        int64_t n_visits, const int64_t *visit_seg,
+                        const int32_t *visit_epoch, int64_t n_seg,
+                        const int64_t *seg_ptr, const int32_t *seg_col,
+                        const int32_t *rec_row, const float *rec_val,
+                        uint8_t *Wc, float *Ws, float *H, int32_t *rec_count,
+                        uint64_t seed) {
+  float *w = (float *)malloc(sizeof(float) * (size_t)k);
+  uint32_t *r16 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)k);
+  if (!w || !r16) { free(w); free(r16); return -2; }
+  for (int64_t v = 0; v < n_visits; ++v) {
+    const int64_t s = visit_seg[v];
+    if (s < 0 || s >= n_seg) { free(w); free(r16); return -1; }
+    const uint32_t e = (uint32_t)visit_epoch[v];
+    float *h = H + (int64_t)seg_col[s] * k;
+    for (int64_t r = seg_ptr[s]; r < seg_ptr[s + 1]; ++r) {
+      const int64_t i = rec_row[r];
+      uint8_t *c = Wc + i * k;
+      for (int32_t l = 0; l < k; ++l) w[l] = Ws[i] * orc_e4m3_to_f32(c[l]);
+      const float step = (float)orc_step_size(alpha, beta, rec_count[r]);
+      orc_sgd_update_f32(k, w, h, rec_val[r], lambda, step);
+      for (int32_t l = 0; l < k; ++l)
+        r16[l] = sr_bits(seed, (uint32_t)r, (uint32_t)((uint64_t)r >> 32), e, 0x57000000u,
+                         l, 0);
+      orc_e4m3_row(k, w, r16, c, &Ws[i]);
+      rec_count[r] += 1;
+    }
+  }
+  free(w);
+  free(r16);
+  return 0;
+}
+
+/* Array forms for the Python side. */
+void orc_e4m3_rn_n(int64_t n, const float *x, uint8_t *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_e4m3_rn(x[i]);
+}
+void orc_e4m3_sr_n(int64_t n, const float *x, const uint32_t *r16, uint8_t *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_e4m3_sr(x[i], r16[i]);
+}
+void orc_e4m3_to_f32_n(int64_t n, const uint8_t *c, float *out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_e4m3_to_f32(c[i]);
+}
+void orc_e4m3_rows(int64_t rows, int32_t k, const float *w, const uint32_t *r16,
+                   uint8_t *codes, float *scale) {
+  for (int64_t i = 0; i < rows; ++i)
+    orc_e4m3_row(k, w + i * k, r16 ? r16 + i * k : NULL, codes + i * k, scale + i);
+}
