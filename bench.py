@@ -381,6 +381,9 @@ def run_sweep(args):
     total = float(sum(nnz))
     wpb = 8
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if len(specs) > sms:
+        raise SystemExit("--sweep %d: at most %d problems (one block each, every block "
+                         "resident)" % (len(specs), sms))
     alpha, beta = 0.012, 0.05
 
     def handles(workers):
