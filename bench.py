@@ -372,6 +372,10 @@ def run_sweep(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if args.sweep > sms:
+        raise SystemExit("--sweep %d: at most %d problems (one block each, every block "
+                         "resident)" % (args.sweep, sms))
     specs = synth.sweep_specs(args.sweep, seed=5)
     t0 = time.perf_counter()
     probs = [synth.sweep_problem(sp, device=dev) for sp in specs]
@@ -380,10 +384,6 @@ def run_sweep(args):
     nnz = [r.nnz for r in probs]
     total = float(sum(nnz))
     wpb = 8
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    if len(specs) > sms:
-        raise SystemExit("--sweep %d: at most %d problems (one block each, every block "
-                         "resident)" % (len(specs), sms))
     alpha, beta = 0.012, 0.05
 
     def handles(workers):
