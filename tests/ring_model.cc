@@ -11,10 +11,24 @@
 // a fresh random order (Sec. 3.4's permutation circulation).  Every wait is
 // bounded; a worker that gives up raises the shared status word.
 //
-// usage: ring_model <p> <n_items> <max_deg> <epochs> <seed> <fault>
+// Two consumer disciplines:
+//  fifo    one token at a time at the ring's head; capacity >= the worker's
+//          segments;
+//  window  the batched kernel's: the first kWindow positions are read, up
+//          to kBatch ready ones are taken (a position reserved but not yet
+//          written does not hold back the ones behind it), the head moves
+//          past the taken prefix, and the batch's tokens are handed on
+//          together at its end; capacity >= segments + kWindow + 1.
+// Every slot also records the lap last taken from it (model instrumentation
+// only), so a producer that would overwrite a token not yet taken is seen.
+//
+// usage: ring_model <p> <n_items> <max_deg> <epochs> <seed> <fault> [mode]
 //   fault: none | drop (one token never sent) | dup (one token sent twice)
 //          | stall (one worker sleeps between visits)
-// prints: status=<ok|timeout|ownership> visits=<v> expected=<S*E>
+//          | slowpub (some producers pause between reserving and writing)
+//          | smallring (rings of a quarter of the segments: a planted mistake)
+//   mode:  fifo (default) | window
+// prints: status=<ok|timeout|ownership|overwrite> visits=<v> expected=<S*E>
 //         exact_once=<0|1> per_item_epochs_ok=<0|1>
 #include <algorithm>
 #include <atomic>
@@ -30,10 +44,14 @@
 
 namespace {
 
+constexpr int kWindow = 16;
+constexpr int kBatch = 8;
+
 struct Model {
   int p = 0, n = 0, epochs = 0;
   uint64_t seed = 0;
   std::string fault;
+  bool window = false;
   // layout: segments per item, each with a worker
   std::vector<int> seg_worker, seg_item;
   std::vector<std::vector<int>> item_segs;    // segments of item j
@@ -42,18 +60,20 @@ struct Model {
   std::vector<int> log2cap;
   std::vector<int64_t> base;
   std::vector<std::atomic<uint64_t>> slots;
+  std::vector<std::atomic<uint32_t>> taken_lap;  // per slot: lap last taken (~0: none)
   std::vector<std::atomic<uint32_t>> tail;
   // token state (owned by the holder)
   std::vector<int> hop, epoch;
   std::vector<std::vector<int>> order;         // current epoch's order per item
   std::vector<std::atomic<int>> owner;
   std::vector<std::atomic<int>> visits;        // per (segment, epoch)
-  std::atomic<int> status{0};                  // 0 ok, 1 timeout, 2 ownership
+  std::atomic<int> status{0};  // 0 ok, 1 timeout, 2 ownership, 3 overwrite
+  std::atomic<uint32_t> pushes{0};
   std::atomic<int64_t> total{0};
 
-  Model(int p_, int n_, int maxdeg, int e_, uint64_t s_, std::string f)
-      : p(p_), n(n_), epochs(e_), seed(s_), fault(std::move(f)),
-        slots(0), tail(p_), owner(n_), visits(0) {
+  Model(int p_, int n_, int maxdeg, int e_, uint64_t s_, std::string f, bool win)
+      : p(p_), n(n_), epochs(e_), seed(s_), fault(std::move(f)), window(win),
+        slots(0), taken_lap(0), tail(p_), owner(n_), visits(0) {
     std::mt19937_64 rng(seed);
     item_segs.resize(n);
     nseg.assign(p, 0);
@@ -73,8 +93,10 @@ struct Model {
     base.resize(p + 1);
     int64_t b = 0;
     for (int q = 0; q < p; ++q) {
+      int need = window ? nseg[q] + kWindow + 1 : nseg[q];
+      if (fault == "smallring") need = nseg[q] / 4;
       int lg = 0;
-      while ((1 << lg) < nseg[q] || lg < 1) ++lg;
+      while ((1 << lg) < need || lg < 1) ++lg;
       log2cap[q] = lg;
       base[q] = b;
       b += int64_t(1) << lg;
@@ -83,6 +105,9 @@ struct Model {
     std::vector<std::atomic<uint64_t>> s(b);
     slots.swap(s);
     for (auto& x : slots) x.store(~0ull);
+    std::vector<std::atomic<uint32_t>> tl(b);
+    taken_lap.swap(tl);
+    for (auto& x : taken_lap) x.store(~0u);
     for (auto& t : tail) t.store(0);
     hop.assign(n, 0);
     epoch.assign(n, 0);
@@ -102,8 +127,16 @@ struct Model {
   void push(int q, int seg) {
     const uint32_t pos = tail[q].fetch_add(1, std::memory_order_relaxed);
     const int lg = log2cap[q];
-    auto& slot = slots[base[q] + (pos & ((1u << lg) - 1u))];
-    slot.store((uint64_t(pos >> lg) << 32) | uint32_t(seg), std::memory_order_release);
+    const int64_t at = base[q] + (pos & ((1u << lg) - 1u));
+    if (fault == "slowpub" && pushes.fetch_add(1) % 5 == 0)
+      std::this_thread::sleep_for(std::chrono::microseconds(150));
+    // the slot's previous lap must have been taken before it is written again
+    const uint32_t lap = pos >> lg;
+    if (lap > 0 && taken_lap[at].load(std::memory_order_acquire) != lap - 1) {
+      int z = 0;
+      status.compare_exchange_strong(z, 3);
+    }
+    slots[at].store((uint64_t(lap) << 32) | uint32_t(seg), std::memory_order_release);
   }
 
   int pop(int q, uint32_t head) {
@@ -113,7 +146,10 @@ struct Model {
     const auto t0 = std::chrono::steady_clock::now();
     for (uint64_t it = 0; it < (1ull << 28); ++it) {
       const uint64_t v = slot.load(std::memory_order_acquire);
-      if (uint32_t(v >> 32) == lap) return int(uint32_t(v));
+      if (uint32_t(v >> 32) == lap) {
+        taken_lap[base[q] + (head & ((1u << lg) - 1u))].store(lap, std::memory_order_release);
+        return int(uint32_t(v));
+      }
       if ((it & 255) == 255) {
         if (status.load(std::memory_order_relaxed) != 0) return -1;
         if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(300)) break;
@@ -125,7 +161,90 @@ struct Model {
     return -1;
   }
 
+  // One visit of segment seg by worker q: ownership check, accounting, the
+  // token's next hop.  Returns the next segment, or -1 after its last epoch.
+  int visit(int q, int seg) {
+    const int j = seg_item[seg];
+    if (owner[j].exchange(q) != -1) {
+      int z = 0;
+      status.compare_exchange_strong(z, 2);
+    }
+    const int e = epoch[j];
+    if (e >= 0 && e < epochs) visits[size_t(seg) * epochs + e].fetch_add(1);
+    total.fetch_add(1);
+    if (fault == "stall" && q == 0)
+      std::this_thread::sleep_for(std::chrono::microseconds(200));
+    int nh = hop[j] + 1, ne = e;
+    if (nh == int(item_segs[j].size())) {
+      nh = 0;
+      ne = e + 1;
+      if (ne < epochs) shuffle_order(j, ne);
+    }
+    hop[j] = nh;
+    epoch[j] = ne;
+    if (owner[j].exchange(-1) != q) {
+      int z = 0;
+      status.compare_exchange_strong(z, 2);
+    }
+    return ne < epochs ? order[j][nh] : -1;
+  }
+
+  // The batched kernel's discipline (see the header comment).
+  void worker_window(int q) {
+    const int64_t quota = int64_t(nseg[q]) * epochs;
+    const int lg = log2cap[q];
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t head = 0, taken = 0;
+    int64_t done = 0;
+    auto t_last = std::chrono::steady_clock::now();
+    while (done < quota) {
+      int got[kWindow];
+      uint32_t ready = 0;
+      for (int i = 0; i < kWindow; ++i) {
+        if ((taken >> i) & 1u) continue;
+        const uint32_t pos = head + uint32_t(i);
+        const uint64_t v = slots[base[q] + (pos & mask)].load(std::memory_order_acquire);
+        if (uint32_t(v >> 32) == (pos >> lg)) {
+          ready |= 1u << i;
+          got[i] = int(uint32_t(v));
+        }
+      }
+      if (!ready) {
+        if (status.load(std::memory_order_relaxed) != 0) return;
+        if (std::chrono::steady_clock::now() - t_last > std::chrono::milliseconds(300)) {
+          int z = 0;
+          status.compare_exchange_strong(z, 1);
+          return;
+        }
+        std::this_thread::yield();
+        continue;
+      }
+      t_last = std::chrono::steady_clock::now();
+      std::vector<int> batch;
+      for (int i = 0; i < kWindow && int(batch.size()) < kBatch; ++i) {
+        if (!((ready >> i) & 1u)) continue;
+        const uint32_t pos = head + uint32_t(i);
+        taken_lap[base[q] + (pos & mask)].store(pos >> lg, std::memory_order_release);
+        taken |= 1u << i;
+        batch.push_back(got[i]);
+      }
+      while (taken & 1u) {  // the head moves past the taken prefix
+        taken >>= 1;
+        ++head;
+      }
+      done += int64_t(batch.size());
+      std::vector<int> next;
+      for (int seg : batch) next.push_back(visit(q, seg));
+      for (int nseg_id : next)  // handed on together at the end of the batch
+        if (nseg_id >= 0) push(seg_worker[nseg_id], nseg_id);
+    }
+  }
+
   void worker(int q) {
+    if (window) {
+      worker_window(q);
+      return;
+    }
     const int64_t quota = int64_t(nseg[q]) * epochs;
     uint32_t head = 0;
     for (int64_t v = 0; v < quota; ++v, ++head) {
@@ -176,12 +295,13 @@ struct Model {
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc != 7) {
-    std::fprintf(stderr, "usage: ring_model p n maxdeg epochs seed fault\n");
+  if (argc != 7 && argc != 8) {
+    std::fprintf(stderr, "usage: ring_model p n maxdeg epochs seed fault [fifo|window]\n");
     return 2;
   }
+  const bool window = argc == 8 && std::string(argv[7]) == "window";
   Model M(std::atoi(argv[1]), std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]),
-          std::strtoull(argv[5], nullptr, 10), argv[6]);
+          std::strtoull(argv[5], nullptr, 10), argv[6], window);
   M.run();
   const int64_t S = int64_t(M.seg_worker.size());
   bool exact = true;
@@ -190,7 +310,10 @@ int main(int argc, char** argv) {
   bool per_item = true;
   for (int j = 0; j < M.n; ++j)
     if (M.epoch[j] != M.epochs || M.hop[j] != 0) per_item = false;
-  const char* st = M.status == 0 ? "ok" : (M.status == 1 ? "timeout" : "ownership");
+  const char* st = M.status == 0   ? "ok"
+                   : M.status == 1 ? "timeout"
+                   : M.status == 2 ? "ownership"
+                                   : "overwrite";
   std::printf("status=%s visits=%lld expected=%lld exact_once=%d per_item_epochs_ok=%d\n", st,
               (long long)M.total.load(), (long long)(S * M.epochs), exact ? 1 : 0,
               per_item ? 1 : 0);

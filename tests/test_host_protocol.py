@@ -2,8 +2,13 @@
 
 ring_model.cc models the ring queues of the persistent kernel with host
 threads (same slot format, reservation and publication order, bounded
-waits).  Failures are made on the host: a token that is never sent, a token
-sent twice, a slow worker.  No GPU is involved.
+waits), under two consumer disciplines: one token at a time at the head
+(fifo), and the batched kernel's window (up to 8 ready tokens taken from the
+first 16 positions, out of order, handed on together at the end of the
+batch, rings with 17 slots of headroom).  Failures are made on the host: a
+token that is never sent, a token sent twice, a slow worker, producers
+pausing between reserving and writing a slot, and (a planted mistake in the
+model) rings too small for the tokens in flight.  No GPU is involved.
 """
 import os
 import subprocess
@@ -21,39 +26,65 @@ def model(tmp_path_factory):
     return exe
 
 
-def run(exe, p, n, maxdeg, epochs, seed, fault):
-    out = subprocess.run([exe, str(p), str(n), str(maxdeg), str(epochs), str(seed), fault],
-                         capture_output=True, text=True, timeout=120, check=True).stdout
+def run(exe, p, n, maxdeg, epochs, seed, fault, mode="fifo"):
+    out = subprocess.run([exe, str(p), str(n), str(maxdeg), str(epochs), str(seed), fault,
+                          mode], capture_output=True, text=True, timeout=120,
+                         check=True).stdout
     return dict(kv.split("=") for kv in out.split())
 
 
+@pytest.mark.parametrize("mode", ["fifo", "window"])
 @pytest.mark.parametrize("p,n,maxdeg,epochs,seed",
                          [(4, 50, 4, 3, 1), (8, 200, 8, 4, 2), (16, 300, 5, 2, 3),
                           (3, 1, 3, 5, 4), (6, 40, 1, 3, 5)])
-def test_protocol_exactly_once(model, p, n, maxdeg, epochs, seed):
+def test_protocol_exactly_once(model, p, n, maxdeg, epochs, seed, mode):
     """Every segment is visited exactly once per epoch, every item finishes
-    all epochs, no token is held twice."""
-    r = run(model, p, n, maxdeg, epochs, seed, "none")
+    all epochs, no token is held twice, no slot is written again before its
+    token was taken."""
+    r = run(model, p, n, maxdeg, epochs, seed, "none", mode)
     assert r["status"] == "ok"
     assert r["visits"] == r["expected"]
     assert r["exact_once"] == "1" and r["per_item_epochs_ok"] == "1"
 
 
-def test_slow_worker_is_still_correct(model):
-    r = run(model, 6, 100, 6, 3, 7, "stall")
+@pytest.mark.parametrize("mode", ["fifo", "window"])
+def test_slow_worker_is_still_correct(model, mode):
+    r = run(model, 6, 100, 6, 3, 7, "stall", mode)
     assert r["status"] == "ok" and r["exact_once"] == "1"
 
 
-def test_dropped_token_is_detected_by_timeout(model):
+@pytest.mark.parametrize("seed", [11, 12, 13])
+@pytest.mark.parametrize("mode", ["fifo", "window"])
+def test_slow_publication_is_still_correct(model, mode, seed):
+    """Producers that pause between reserving a position and writing it:
+    the window takes the ready tokens behind the reserved one, the head
+    waits for it, and the 17 slots of headroom keep every slot from being
+    written again before it was taken."""
+    r = run(model, 12, 400, 12, 3, seed, "slowpub", mode)
+    assert r["status"] == "ok", r
+    assert r["visits"] == r["expected"] and r["exact_once"] == "1"
+
+
+@pytest.mark.parametrize("mode", ["fifo", "window"])
+def test_too_small_rings_are_detected(model, mode):
+    """A planted mistake in the model (rings of a quarter of the segments):
+    a producer about to overwrite a token not yet taken is seen."""
+    r = run(model, 4, 200, 4, 3, 1, "smallring", mode)
+    assert r["status"] == "overwrite" and r["exact_once"] == "0"
+
+
+@pytest.mark.parametrize("mode", ["fifo", "window"])
+def test_dropped_token_is_detected_by_timeout(model, mode):
     """A lost message: the bounded wait gives up and the status says so; the
     accounting shows the missing visits."""
-    r = run(model, 4, 30, 4, 2, 8, "drop")
+    r = run(model, 4, 30, 4, 2, 8, "drop", mode)
     assert r["status"] == "timeout"
     assert int(r["visits"]) < int(r["expected"]) and r["exact_once"] == "0"
 
 
-def test_duplicated_token_is_detected(model):
+@pytest.mark.parametrize("mode", ["fifo", "window"])
+def test_duplicated_token_is_detected(model, mode):
     """A duplicated message breaks exactly-once: two owners of one item, or a
     visit count other than one, or a worker starved of its quota."""
-    r = run(model, 4, 30, 4, 2, 9, "dup")
+    r = run(model, 4, 30, 4, 2, 9, "dup", mode)
     assert r["status"] in ("ownership", "timeout") or r["exact_once"] == "0"
