@@ -18,7 +18,11 @@
 //          to kBatch ready ones are taken (a position reserved but not yet
 //          written does not hold back the ones behind it), the head moves
 //          past the taken prefix, and the batch's tokens are handed on
-//          together at its end; capacity >= segments + kWindow + 1.
+//          together at its end; capacity >= segments + kWindow + 1.  The
+//          tokens of urgent items (at least half the segments of the
+//          item with most) travel through a second ring per worker
+//          (capacity >= urgent items + 1), taken one at a time before each
+//          batch and before each visit of a batch, and handed on at once.
 // Every slot also records the lap last taken from it (model instrumentation
 // only), so a producer that would overwrite a token not yet taken is seen.
 //
@@ -29,7 +33,7 @@
 //          | smallring (rings of a quarter of the segments: a planted mistake)
 //   mode:  fifo (default) | window
 // prints: status=<ok|timeout|ownership|overwrite> visits=<v> expected=<S*E>
-//         exact_once=<0|1> per_item_epochs_ok=<0|1>
+//         exact_once=<0|1> per_item_epochs_ok=<0|1> urgent_items=<u>
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -61,6 +65,12 @@ struct Model {
   std::vector<int64_t> base;
   std::vector<std::atomic<uint64_t>> slots;
   std::vector<std::atomic<uint32_t>> taken_lap;  // per slot: lap last taken (~0: none)
+  // urgent rings (window discipline only): p rings of 2^lgu slots
+  std::vector<char> urgent;
+  int lgu = 5;
+  std::vector<std::atomic<uint64_t>> uslots;
+  std::vector<std::atomic<uint32_t>> utail;
+  std::vector<std::atomic<uint32_t>> utaken_lap;
   std::vector<std::atomic<uint32_t>> tail;
   // token state (owned by the holder)
   std::vector<int> hop, epoch;
@@ -73,7 +83,8 @@ struct Model {
 
   Model(int p_, int n_, int maxdeg, int e_, uint64_t s_, std::string f, bool win)
       : p(p_), n(n_), epochs(e_), seed(s_), fault(std::move(f)), window(win),
-        slots(0), taken_lap(0), tail(p_), owner(n_), visits(0) {
+        slots(0), taken_lap(0), uslots(0), utail(p_), utaken_lap(0), tail(p_), owner(n_),
+        visits(0) {
     std::mt19937_64 rng(seed);
     item_segs.resize(n);
     nseg.assign(p, 0);
@@ -108,6 +119,25 @@ struct Model {
     std::vector<std::atomic<uint32_t>> tl(b);
     taken_lap.swap(tl);
     for (auto& x : taken_lap) x.store(~0u);
+    size_t maxd = 0;
+    for (auto& v : item_segs) maxd = std::max(maxd, v.size());
+    urgent.assign(n, 0);
+    int n_urgent = 0;
+    for (int j = 0; j < n; ++j)
+      if (window && 2 * item_segs[j].size() >= maxd) {
+        urgent[j] = 1;
+        ++n_urgent;
+      }
+    int need_u = n_urgent + 1;
+    if (fault == "smallring") need_u = std::max(1, n_urgent / 4);
+    while ((1 << lgu) < need_u) ++lgu;
+    std::vector<std::atomic<uint64_t>> us(size_t(p) << lgu);
+    uslots.swap(us);
+    for (auto& x : uslots) x.store(~0ull);
+    std::vector<std::atomic<uint32_t>> utl(size_t(p) << lgu);
+    utaken_lap.swap(utl);
+    for (auto& x : utaken_lap) x.store(~0u);
+    for (auto& t : utail) t.store(0);
     for (auto& t : tail) t.store(0);
     hop.assign(n, 0);
     epoch.assign(n, 0);
@@ -125,18 +155,21 @@ struct Model {
   }
 
   void push(int q, int seg) {
-    const uint32_t pos = tail[q].fetch_add(1, std::memory_order_relaxed);
-    const int lg = log2cap[q];
-    const int64_t at = base[q] + (pos & ((1u << lg) - 1u));
+    const bool u = urgent[seg_item[seg]] != 0;
+    const uint32_t pos = (u ? utail[q] : tail[q]).fetch_add(1, std::memory_order_relaxed);
+    const int lg = u ? lgu : log2cap[q];
+    const int64_t at = (u ? (int64_t(q) << lgu) : base[q]) + (pos & ((1u << lg) - 1u));
+    auto& tlap = u ? utaken_lap[at] : taken_lap[at];
+    auto& slot = u ? uslots[at] : slots[at];
     if (fault == "slowpub" && pushes.fetch_add(1) % 5 == 0)
       std::this_thread::sleep_for(std::chrono::microseconds(150));
     // the slot's previous lap must have been taken before it is written again
     const uint32_t lap = pos >> lg;
-    if (lap > 0 && taken_lap[at].load(std::memory_order_acquire) != lap - 1) {
+    if (lap > 0 && tlap.load(std::memory_order_acquire) != lap - 1) {
       int z = 0;
       status.compare_exchange_strong(z, 3);
     }
-    slots[at].store((uint64_t(lap) << 32) | uint32_t(seg), std::memory_order_release);
+    slot.store((uint64_t(lap) << 32) | uint32_t(seg), std::memory_order_release);
   }
 
   int pop(int q, uint32_t head) {
@@ -194,10 +227,27 @@ struct Model {
     const int64_t quota = int64_t(nseg[q]) * epochs;
     const int lg = log2cap[q];
     const uint32_t mask = (1u << lg) - 1u;
-    uint32_t head = 0, taken = 0;
+    uint32_t head = 0, taken = 0, head_u = 0;
     int64_t done = 0;
     auto t_last = std::chrono::steady_clock::now();
+    // an urgent token waiting at the head of the urgent ring: visited and
+    // handed on at once
+    auto try_urgent = [&]() -> bool {
+      const int64_t at = (int64_t(q) << lgu) + (head_u & ((1u << lgu) - 1u));
+      const uint64_t v = uslots[at].load(std::memory_order_acquire);
+      if (uint32_t(v >> 32) != (head_u >> lgu)) return false;
+      utaken_lap[at].store(head_u >> lgu, std::memory_order_release);
+      ++head_u;
+      ++done;
+      const int nx = visit(q, int(uint32_t(v)));
+      if (nx >= 0) push(seg_worker[nx], nx);
+      t_last = std::chrono::steady_clock::now();
+      return true;
+    };
     while (done < quota) {
+      while (done < quota && try_urgent()) {
+      }
+      if (done >= quota) break;
       int got[kWindow];
       uint32_t ready = 0;
       for (int i = 0; i < kWindow; ++i) {
@@ -234,7 +284,11 @@ struct Model {
       }
       done += int64_t(batch.size());
       std::vector<int> next;
-      for (int seg : batch) next.push_back(visit(q, seg));
+      for (int seg : batch) {
+        while (try_urgent()) {
+        }
+        next.push_back(visit(q, seg));
+      }
       for (int nseg_id : next)  // handed on together at the end of the batch
         if (nseg_id >= 0) push(seg_worker[nseg_id], nseg_id);
     }
@@ -281,7 +335,7 @@ struct Model {
 
   void run() {
     for (int j = 0; j < n; ++j) {
-      shuffle_order(j, 0);
+      shuffle_order(j, 0);  // (push() routes urgent items to the urgent rings)
       if (fault == "drop" && j == 0) continue;
       push(seg_worker[order[j][0]], order[j][0]);
       if (fault == "dup" && j == 0) push(seg_worker[order[j][0]], order[j][0]);
@@ -314,8 +368,11 @@ int main(int argc, char** argv) {
                    : M.status == 1 ? "timeout"
                    : M.status == 2 ? "ownership"
                                    : "overwrite";
-  std::printf("status=%s visits=%lld expected=%lld exact_once=%d per_item_epochs_ok=%d\n", st,
-              (long long)M.total.load(), (long long)(S * M.epochs), exact ? 1 : 0,
-              per_item ? 1 : 0);
+  int n_urgent = 0;
+  for (char u : M.urgent) n_urgent += u;
+  std::printf(
+      "status=%s visits=%lld expected=%lld exact_once=%d per_item_epochs_ok=%d urgent_items=%d\n",
+      st, (long long)M.total.load(), (long long)(S * M.epochs), exact ? 1 : 0, per_item ? 1 : 0,
+      n_urgent);
   return 0;
 }

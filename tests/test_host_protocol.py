@@ -5,7 +5,8 @@ threads (same slot format, reservation and publication order, bounded
 waits), under two consumer disciplines: one token at a time at the head
 (fifo), and the batched kernel's window (up to 8 ready tokens taken from the
 first 16 positions, out of order, handed on together at the end of the
-batch, rings with 17 slots of headroom).  Failures are made on the host: a
+batch, rings with 17 slots of headroom; the tokens of the most-visited
+items through a second, urgent ring per worker, taken between visits).  Failures are made on the host: a
 token that is never sent, a token sent twice, a slow worker, producers
 pausing between reserving and writing a slot, and (a planted mistake in the
 model) rings too small for the tokens in flight.  No GPU is involved.
@@ -42,6 +43,9 @@ def test_protocol_exactly_once(model, p, n, maxdeg, epochs, seed, mode):
     all epochs, no token is held twice, no slot is written again before its
     token was taken."""
     r = run(model, p, n, maxdeg, epochs, seed, "none", mode)
+    # the window discipline routes the most-visited items through the
+    # urgent rings
+    assert (int(r["urgent_items"]) > 0) == (mode == "window")
     assert r["status"] == "ok"
     assert r["visits"] == r["expected"]
     assert r["exact_once"] == "1" and r["per_item_epochs_ok"] == "1"
