@@ -90,6 +90,15 @@ def test_host_only_entry_points(lib):
         nb.NOMAD_ERR_INVALID_ARG
     assert not h.value
     assert cdll.nomad_epoch(None, 1, None) == nb.NOMAD_ERR_INVALID_ARG
+    # several problems: no array, no handles, a NULL handle
+    assert cdll.nomad_epoch_many(None, 1, 1, None) == nb.NOMAD_ERR_INVALID_ARG
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert cdll.nomad_epoch_many(arr, 0, 1, None) == nb.NOMAD_ERR_INVALID_ARG
+    assert cdll.nomad_epoch_many(arr, 2, 1, None) == nb.NOMAD_ERR_INVALID_ARG
+    ns = ctypes.c_int64(-1)
+    assert cdll.nomad_last_epoch_span_ns(None, ctypes.byref(ns), None) == \
+        nb.NOMAD_ERR_INVALID_ARG
+    assert ns.value == -1
     cdll.nomad_destroy(None)
 
 
