@@ -39,3 +39,17 @@ def test_chunked_generation_is_a_valid_split(monkeypatch):
         qa = np.quantile(np.bincount(a, minlength=size), [0.5, 0.9, 0.99, 1.0])
         qb = np.quantile(np.bincount(b, minlength=size), [0.5, 0.9, 0.99, 1.0])
         assert np.all(np.abs(qa - qb) <= 0.15 * qb + 2), (qa, qb)
+
+
+@pytest.mark.parametrize("k", [16, 128])
+def test_sweep_problem_follows_its_recipe(k):
+    """A sweep problem is a planted rank-k matrix: <u_i, v_j> has unit
+    variance and the noise is N(0, 0.1^2), so the values have mean ~0 and
+    variance ~1.01; density*m*n distinct entries, 1% held out."""
+    r = synth.sweep_problem(dict(m=4000, n=2000, density=0.01, k=k, lam=0.1, seed=3))
+    tr, tc, tv, er, ec, ev = r.numpy()
+    v = np.concatenate([tv, ev]).astype(np.float64)
+    assert v.size == 80000
+    assert abs(er.size - 800) <= 8
+    assert abs(v.mean()) < 0.03
+    assert 0.9 < v.var() < 1.15, v.var()
