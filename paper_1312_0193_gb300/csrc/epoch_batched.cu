@@ -5,27 +5,37 @@
 // circulation of Sec. 3.4), organised so that the latency of global memory is
 // paid per batch of tokens instead of per visit:
 //
-//  1. take the ready prefix of the own ring (up to Batch<CPL> tokens) with one
-//     acquire load per lane;
-//  2. fetch every token's metadata lane-parallel (lane b = token b);
-//  3. order the visits: long visits (>= kHeavy ratings, the items whose
-//     serial chain through h_j is longest) first, then the rest;
+//  1. take the ready tokens among the first kRingWindow positions of the own
+//     ring (up to Batch<CPL>; a position reserved but not yet written does
+//     not hold back the ones behind it), one acquire load per lane;
+//  2. read every token's record of its next visit (written by the previous
+//     holder before its push) lane-parallel, lane b = token b;
+//  3. order the visits: long visits (>= kHeavy ratings) first, then the
+//     rest in ring order;
 //  4. copy every h_j of the batch into shared memory and the rating records
 //     of the batch, as one stream of positions, into a shared circular
-//     buffer (cp.async);
-//  5. walk the stream: W rows are copied into a ring of R shared-memory
-//     slots R-1 positions ahead of the update (cp.async), so up to R-1 rows
-//     per worker are in flight; the update itself is the fused SGD step of
-//     Eq. w_update / h_update (descent sign, old w_i in the h update);
-//  6. push long visits' tokens right after their visit, the others together
-//     at the end of the batch (one fence, lane-parallel reservations).
+//     buffer (cp.async); compute each token's next hop meanwhile;
+//  5. run the long visits in block form (long_visit), each token handed on
+//     right after its visit;
+//  6. walk the stream of short visits: W rows are copied into a ring of R
+//     shared-memory slots R-1 positions ahead of the update (cp.async); the
+//     update itself is the fused SGD step of Eq. w_update / h_update
+//     (descent sign, old w_i in the h update);
+//  7. hand on the remaining tokens together: one __syncwarp, then one
+//     release store per token lane.
+//
+// The tokens of the items with most ratings travel through a second, urgent
+// ring per worker and are visited out of turn between visits (urgent_visit);
+// visits are never split, so the serial order stays a valid NOMAD order.
 //
 // A row can appear in two visits of one batch (a user who rated both items).
-// Its copy for the later visit must not be taken before the earlier visit
-// has written it: when the row of the position being prefetched equals the
-// row of a position still in the prefetch window, no copy is made and the
-// update loads the row from global memory after the earlier store (same
-// thread, program order).
+// Its copy for the later position must not be taken before the earlier
+// position has updated it: when the row being prefetched is the row of a
+// position still in flight, no copy is made, and the latest such position
+// writes its updated row into the later position's slot as well.
+//
+// The worker body is shared by the one-problem kernel and a form that runs
+// several independent problems in one launch (nomad_batched_many_kernel).
 #include "sgd_common.cuh"
 
 namespace nomad {
