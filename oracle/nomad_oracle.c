@@ -464,11 +464,9 @@ float orc_bf16_to_f32(uint16_t b) { return bits_f32((uint32_t)b << 16); }
 /* The 16 random bits for entry l of a row written back by the update of
  * record r in epoch e (factor W) or by the end of the visit of segment s in
  * epoch e (factor H): Philox4x32-10 with key = seed and counter
- * (p_lo, p_hi, e, 0x57000000 | l/4) for W, where p = floor(r/2) numbers the
- * pair of records (2p, 2p+1) that shares one draw, and (s, e, 0,
- * 0x48000000 | l/4) for H.  Entry l takes word (l mod 4)/2 of the draw for
- * an even record and word 2 + (l mod 4)/2 for an odd one (W), or word
- * 2 + (l mod 4)/2 (H); its low half for even l and high half for odd l. */
+ * (r_lo, r_hi, e, 0x57000000 | l/4) for W, (s, e, 0, 0x48000000 | l/4) for
+ * H; entry l takes word (l mod 4)/2 (W) or 2 + (l mod 4)/2 (H), its low half
+ * for even l and high half for odd l. */
 static uint32_t sr_bits(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                         uint32_t tag, int32_t l, int word_base) {
   uint32_t w = rand_word(seed, c0, c1, c2, tag | (uint32_t)(l / 4),
@@ -505,9 +503,9 @@ int32_t orc_replay_bf16(int32_t k, float lambda, double alpha, double beta,
       const float step = (float)orc_step_size(alpha, beta, rec_count[r]);
       orc_sgd_update_f32(k, w, h, rec_val[r], lambda, step);
       for (int32_t l = 0; l < k; ++l)
-        wb[l] = orc_bf16_sr(w[l], sr_bits(seed, (uint32_t)(r >> 1),
-                                          (uint32_t)((uint64_t)r >> 33), e,
-                                          0x57000000u, l, 2 * (int)(r & 1)));
+        wb[l] = orc_bf16_sr(w[l], sr_bits(seed, (uint32_t)r,
+                                          (uint32_t)((uint64_t)r >> 32), e,
+                                          0x57000000u, l, 0));
       rec_count[r] += 1;
     }
     for (int32_t l = 0; l < k; ++l)
@@ -641,8 +639,8 @@ int32_t orc_replay_e4m3(int32_t k, float lambda, double alpha, double beta,
       const float step = (float)orc_step_size(alpha, beta, rec_count[r]);
       orc_sgd_update_f32(k, w, h, rec_val[r], lambda, step);
       for (int32_t l = 0; l < k; ++l)
-        r16[l] = sr_bits(seed, (uint32_t)(r >> 1), (uint32_t)((uint64_t)r >> 33), e,
-                         0x57000000u, l, 2 * (int)(r & 1));
+        r16[l] = sr_bits(seed, (uint32_t)r, (uint32_t)((uint64_t)r >> 32), e, 0x57000000u,
+                         l, 0);
       orc_e4m3_row(k, w, r16, c, &Ws[i]);
       rec_count[r] += 1;
     }
