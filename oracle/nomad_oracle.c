@@ -461,16 +461,28 @@ uint16_t orc_bf16_sr(float x, uint32_t r16) {
 
 float orc_bf16_to_f32(uint16_t b) { return bits_f32((uint32_t)b << 16); }
 
-/* The 16 random bits for entry l of a row written back by the update of
- * record r in epoch e (factor W) or by the end of the visit of segment s in
- * epoch e (factor H): Philox4x32-10 with key = seed and counter
- * (r_lo, r_hi, e, 0x57000000 | l/4) for W, (s, e, 0, 0x48000000 | l/4) for
- * H; entry l takes word (l mod 4)/2 (W) or 2 + (l mod 4)/2 (H), its low half
- * for even l and high half for odd l. */
+/* The 16 random bits for entry l of a row written back by the end of the
+ * visit of segment s in epoch e (factor H): Philox4x32-10 with key = seed
+ * and counter (s, e, 0, 0x48000000 | l/4); entry l takes word
+ * 2 + (l mod 4)/2, its low half for even l and high half for odd l. */
 static uint32_t sr_bits(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                         uint32_t tag, int32_t l, int word_base) {
   uint32_t w = rand_word(seed, c0, c1, c2, tag | (uint32_t)(l / 4),
                          word_base + (l % 4) / 2);
+  return (l % 2) ? (w >> 16) : (w & 0xffffu);
+}
+
+/* The 16 random bits for entry l of the W row written back by the update of
+ * record r in epoch e.  Entries come in chunks of four (chunk c = l/4), and
+ * one Philox4x32-10 draw with key = seed and counter
+ * (r_lo, r_hi, e, 0x57000000 | c/2) serves the pair of chunks (2q, 2q+1):
+ * chunk c takes words 2(c mod 2) and 2(c mod 2) + 1, entry l word
+ * 2(c mod 2) + (l mod 4)/2, its low half for even l and high half for odd
+ * l. */
+static uint32_t sr_bits_w(uint64_t seed, int64_t r, uint32_t e, int32_t l) {
+  const int32_t c = l / 4;
+  uint32_t w = rand_word(seed, (uint32_t)r, (uint32_t)((uint64_t)r >> 32), e,
+                         0x57000000u | (uint32_t)(c / 2), 2 * (c % 2) + (l % 4) / 2);
   return (l % 2) ? (w >> 16) : (w & 0xffffu);
 }
 
@@ -503,9 +515,7 @@ int32_t orc_replay_bf16(int32_t k, float lambda, double alpha, double beta,
       const float step = (float)orc_step_size(alpha, beta, rec_count[r]);
       orc_sgd_update_f32(k, w, h, rec_val[r], lambda, step);
       for (int32_t l = 0; l < k; ++l)
-        wb[l] = orc_bf16_sr(w[l], sr_bits(seed, (uint32_t)r,
-                                          (uint32_t)((uint64_t)r >> 32), e,
-                                          0x57000000u, l, 0));
+        wb[l] = orc_bf16_sr(w[l], sr_bits_w(seed, r, e, l));
       rec_count[r] += 1;
     }
     for (int32_t l = 0; l < k; ++l)
@@ -639,8 +649,7 @@ int32_t orc_replay_e4m3(int32_t k, float lambda, double alpha, double beta,
       const float step = (float)orc_step_size(alpha, beta, rec_count[r]);
       orc_sgd_update_f32(k, w, h, rec_val[r], lambda, step);
       for (int32_t l = 0; l < k; ++l)
-        r16[l] = sr_bits(seed, (uint32_t)r, (uint32_t)((uint64_t)r >> 32), e, 0x57000000u,
-                         l, 0);
+        r16[l] = sr_bits_w(seed, r, e, l);
       orc_e4m3_row(k, w, r16, c, &Ws[i]);
       rec_count[r] += 1;
     }
