@@ -177,6 +177,29 @@ def workload_name(r, k):
         r.name, r.m, r.n, r.nnz, int(r.test_rows.numel()), k)
 
 
+def host_cpu():
+    """(logical CPUs, CPU model name) of the host running the oracle."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return os.cpu_count(), model or "unknown"
+
+
 def cpu_sample_run(r, k, lam, alpha, beta, target_updates: int, seed: int = 5):
     """The CPU oracle (binary64 shuffled SGD, one thread) for one epoch over a
     sample of the workload: the ratings of every `stride`-th user.  Returns
@@ -270,7 +293,9 @@ def run_ours(args):
     e2e_t, e2e_units = reduce_max_sum(e2e_local, float(nnz) * e2e_steps, world, dev)
     h2d = 12 * nnz + 12 * int(te_r.numel())
 
-    bytes_per_update = 2 * k * (2 if args.precision == "bf16" else 4) + 8
+    # w_i read and written (FP8: codes and the row's scale) + the rating record
+    bytes_per_update = (2 * k * 4 + 8 if args.precision == "fp32" else
+                        2 * k * 2 + 8 if args.precision == "bf16" else 2 * k + 2 * 4 + 8)
     kern_avg_s = statistics.mean(kernel_ms) / 1000.0
     achieved_gbs = nnz * bytes_per_update / kern_avg_s / 1e9
     peak, peak_src = load_peaks()
@@ -294,8 +319,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         upd, secs, desc = cpu_sample_run(r, k, lam, alpha, beta, args.cpu_sample)
+        nproc, model = host_cpu()
         cpu = {"value": upd / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": desc, "seconds": round(secs, 2)}
+               "sample": desc, "seconds": round(secs, 2), "host_nproc": nproc,
+               "host_cpu": model}
 
     if rank == 0:
         out = {
@@ -303,7 +330,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max * 1000.0 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16-storage/f32",
+            "dtype": {"fp32": "f32", "bf16": "bf16-storage/f32",
+                      "fp8": "e4m3-storage(W)/f32"}[args.precision],
             "data": "synthetic (seeded; stands in for the paper's dataset)",
             "config": {
                 "workload": workload_name(r, k), "lambda": lam, "alpha": alpha,
@@ -316,7 +344,7 @@ def run_ours(args):
                 "step": "one epoch (all ratings) + test RMSE",
                 "l2": "inputs larger than L2 (ratings %.0f MB, W %.0f MB); no flush" % (
                     nnz * 8 / 1e6,
-                    r.m * info["pitch"] * (2 if args.precision == "bf16" else 4) / 1e6),
+                    r.m * info["pitch"] * {"fp32": 4, "bf16": 2, "fp8": 1}[args.precision] / 1e6),
                 "parallelism": "replicas x%d (one independent problem per GPU)" % world,
                 "load_seconds_first": round(load_s, 3),
             },
@@ -555,6 +583,49 @@ def time_to_target(args, dev, local):
     return out
 
 
+def run_gaps(args):
+    """Test-RMSE gap to the binary64 oracle per workload and storage format:
+    every workload of tests/golden/rmse_targets.json (data generated on the
+    CPU from its seed, as the oracle's target script did), E epochs of the
+    timed kernel from the library's initial factors, against the oracle's
+    test RMSE after the same E epochs.  One JSON line per (workload,
+    format), then a summary line."""
+    import torch
+    import synth
+    from paper_1312_0193_gb300 import Nomad
+    dev = torch.device("cuda", 0)
+    with open(os.path.join(ROOT, "tests", "golden", "rmse_targets.json")) as f:
+        targets = json.load(f)
+    gens = {"netflix": "netflix_shaped", "yahoo": "yahoo_shaped",
+            "hugewiki": "hugewiki_shaped", "hugewiki-flat": "hugewiki_flat"}
+    rows = []
+    for key in sorted(targets):
+        t = targets[key]
+        if t["config"] not in gens:
+            continue
+        r = getattr(synth, gens[t["config"]])(t["scale"], device="cpu").to(dev)
+        for prec in ("fp32", "bf16", "fp8"):
+            nm = Nomad(r.m, r.n, t["k"], t["lambda"], alpha=t["alpha"], beta=t["beta"],
+                       seed=int(t["init_seed"]), precision=prec)
+            nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
+            ms = 0.0
+            for _ in range(int(t["epochs"])):
+                nm.epoch(1)
+                ms += nm.last_epoch_kernel_ms()
+            nm.check()
+            got = nm.rmse(r.test_rows, r.test_cols, r.test_vals)
+            nm.close()
+            want = float(t["test_rmse"][-1])
+            row = {"workload": t["workload"], "nnz_train": t["nnz_train"], "precision": prec,
+                   "epochs": int(t["epochs"]), "gpu_test_rmse": got, "oracle_test_rmse": want,
+                   "gap_pct": 100.0 * (got / want - 1.0), "gpu_seconds": ms / 1e3}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        del r
+        release_cache(dev)
+    print(json.dumps({"rmse_gaps": rows}), flush=True)
+
+
 def kernel_rev():
     """Hash of the batched worker kernel's sources, to tie profile figures
     to the code they were taken from."""
@@ -575,7 +646,8 @@ def run_reference(args):
     import torch
     dev = torch.device("cuda", local) if torch.cuda.is_available() else "cpu"
     r, k, lam, alpha, beta = make_workload(args.config, dev, args.scale)
-    per_step = max(1, args.ref_sample)
+    # the same sample as the cpu_baseline leg of our arm (--cpu-sample)
+    per_step = max(1, args.ref_sample if args.ref_sample > 0 else args.cpu_sample)
     for _ in range(args.warmup):
         cpu_sample_run(r, k, lam, alpha, beta, per_step // 4)
     tot_u, tot_t, desc = 0, 0.0, ""
@@ -593,7 +665,8 @@ def run_reference(args):
         "config": {"workload": workload_name(r, k), "lambda": lam, "alpha": alpha,
                    "beta": beta},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc, "host_nproc": host_cpu()[0],
+                         "host_cpu": host_cpu()[1]},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -607,7 +680,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="netflix")
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32")
     ap.add_argument("--mode", choices=["epoch", "uniform"], default="epoch",
                     help="routing of tokens: permutation circulation or Alg. 1")
     ap.add_argument("--routing", choices=["uniform", "shorter"], default="uniform",
@@ -619,8 +692,9 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=25_000_000,
                     help="ratings in the CPU-oracle baseline sample")
-    ap.add_argument("--ref-sample", type=int, default=2_000_000,
-                    help="ratings per step of the reference arm")
+    ap.add_argument("--ref-sample", type=int, default=0,
+                    help="ratings per step of the reference arm (0: --cpu-sample, the "
+                         "cpu_baseline leg's sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target leg")
     ap.add_argument("--ttt-scale", type=float, default=0.1,
@@ -629,11 +703,15 @@ def main(argv=None):
                     help="time N independent problems in one launch against N launches")
     ap.add_argument("--sweep-tune", type=int, default=2,
                     help="rounds of block re-allocation from measured per-problem spans")
+    ap.add_argument("--gaps", action="store_true",
+                    help="test-RMSE gap to the oracle for every golden workload and format")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.gaps:
+        run_gaps(args)
     elif args.sweep > 0:
         run_sweep(args)
     else:

@@ -67,6 +67,13 @@ extern "C" {
 #define NOMAD_FP32 0 /* W, H stored in binary32 */
 #define NOMAD_BF16 1 /* W, H stored in bfloat16, FP32 arithmetic, stochastic
                         rounding on write-back */
+#define NOMAD_FP8 2  /* W stored as FP8-E4M3 codes with one binary32 scale
+                        per row (scale = the row's largest magnitude / 448),
+                        H in binary32; FP32 arithmetic; W rounded
+                        stochastically at every update.  The paper has no
+                        such format: this is the capacity variant for the
+                        largest shapes (Hugewiki-sized W: 5 GB instead of
+                        20 GB).  Batched epoch-mode kernel only. */
 
 #define NOMAD_PARTITION_RATINGS 0 /* blocks with equal numbers of ratings
                                      (footnote of Sec. 3.1) */
@@ -92,7 +99,7 @@ typedef struct nomad_schedule {
   float alpha;      /* step size s_t = alpha / (1 + beta t^1.5), Sec. 5.1 */
   float beta;       /* Eq. stepsize_method; Table 1 gives (alpha, beta) */
   int32_t mode;     /* NOMAD_MODE_* */
-  int32_t precision;/* NOMAD_FP32 or NOMAD_BF16 */
+  int32_t precision;/* NOMAD_FP32, NOMAD_BF16 or NOMAD_FP8 */
   int32_t partition;/* NOMAD_PARTITION_* */
   int32_t n_workers;/* p; 0 = every warp the persistent kernel can keep
                        resident on the device */
@@ -215,14 +222,16 @@ NOMAD_API int nomad_rmse(nomad_t *h, int64_t nnz, const int32_t *rows,
 NOMAD_API int nomad_objective(nomad_t *h, double *out, void *stream);
 
 /* Copy the factors out as dense row-major binary32 arrays W[m*k], H[n*k]
- * (BF16 storage is widened exactly).  Either pointer may be NULL.
- * Synchronous. */
+ * (BF16 storage is widened exactly; an E4M3 row is scale * code value, one
+ * binary32 product per entry).  Either pointer may be NULL.  Synchronous. */
 NOMAD_API int nomad_get_factors(nomad_t *h, float *W, float *H, int32_t device_ptrs,
                       void *stream);
 
 /* Replace the factors (checkpoint resume); epochs_done is set to
  * `epochs_done` so that the step-size schedule continues from there.
- * BF16 storage rounds to nearest.  Either pointer may be NULL. Synchronous. */
+ * BF16 storage rounds to nearest; E4M3 storage takes each row's scale from
+ * its largest magnitude and rounds the codes to nearest.  Either pointer may
+ * be NULL. Synchronous. */
 NOMAD_API int nomad_set_factors(nomad_t *h, const float *W, const float *H,
                       int32_t device_ptrs, int64_t epochs_done, void *stream);
 
@@ -273,13 +282,20 @@ NOMAD_API int nomad_get_debug_counts(nomad_t *h, int32_t *rec_count,
  *  out: one double in device memory; receives sqrt(sum (A_ij -
  *    <w_i,h_j>)^2 / nnz) (binary32 residuals, binary64 sums), or NaN when
  *    nnz is 0 or an index lies outside [0,m) x [0,n).
+ * The result equals nomad_rmse's on the same factors up to the order of the
+ * binary64 additions (within about 1e-6 relative), and is the same from call
+ * to call for the same inputs.
  * Asynchronous on `stream` (a cudaStream_t as void*), on the current device.
  * Rejects nnz > NOMAD_NOALLOC_MAX_TILES * 8192 (536,870,912) with
  * NOMAD_ERR_INVALID_ARG.  The first call on a device looks up the scratch
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the scratch array: calls
- * whose work may overlap on the GPU (unordered streams) race and must not
- * be issued. */
+ * call before any stream capture.  The address is looked up again after the
+ * device's context changes (e.g. after cudaDeviceReset).  All calls share
+ * the scratch array: calls whose work may overlap on the GPU (unordered
+ * streams) race and must not be issued.  A CUDA error already pending when
+ * the call starts (from the caller's earlier work) makes it return
+ * NOMAD_ERR_CUDA without launching anything; the pending error is left for
+ * the caller to read. */
 NOMAD_API int nomad_rmse_noalloc(const float *W, const float *H, int64_t m,
                                  int64_t n, int32_t k, int64_t pitch,
                                  int64_t nnz, const int32_t *rows,

@@ -11,6 +11,9 @@ default seed 1), with Table 1's hyperparameters. It records the test RMSE
 (Sec. 5.1) after every epoch.
 
     python -m oracle.targets --config netflix --scale 0.1 --epochs 20
+
+Long runs can write to a file of their own (--out) and be merged into the
+targets file afterwards (--merge a.json b.json ...).
 """
 from __future__ import annotations
 
@@ -31,6 +34,8 @@ TARGETS = os.path.join(os.path.dirname(HERE), "tests", "golden", "rmse_targets.j
 CONFIGS = {
     "netflix": ("netflix_shaped", 100, 0.05, 0.012, 0.05),
     "yahoo": ("yahoo_shaped", 100, 1.0, 0.00075, 0.01),
+    "hugewiki": ("hugewiki_shaped", 100, 0.01, 0.001, 0.0),
+    "hugewiki-flat": ("hugewiki_flat", 100, 0.01, 0.001, 0.0),
     "tiny": ("tiny_planted", 10, 0.05, 0.012, 0.05),
 }
 
@@ -68,6 +73,7 @@ def compute(config: str, scale: float, epochs: int, init_seed: int = 1,
         rmses.append(oracle.rmse(er, ec, ev, W, H))
     return dict(config=config, scale=scale, workload=r.name, m=r.m, n=r.n,
                 nnz_train=int(tr.size), nnz_test=int(er.size), k=k,
+                fingerprint=r.fingerprint(),
                 **{"lambda": lam}, alpha=alpha, beta=beta, init_seed=init_seed,
                 order="shuffled SGD (binary64), seeds %d.." % order_seed,
                 epochs=epochs, test_rmse=rmses,
@@ -80,12 +86,30 @@ def main(argv=None):
     ap.add_argument("--config", choices=sorted(CONFIGS), default="netflix")
     ap.add_argument("--scale", type=float, default=0.1)
     ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--out", default=None,
+                    help="write this one result to a file instead of merging it into "
+                         "tests/golden/rmse_targets.json")
+    ap.add_argument("--merge", nargs="*", default=None,
+                    help="merge result files written with --out into the targets file")
     a = ap.parse_args(argv)
+    if a.merge is not None:
+        allr = load()
+        for path in a.merge:
+            with open(path) as f:
+                res = json.load(f)
+            allr[key(res["config"], res["scale"])] = res
+        with open(TARGETS, "w") as f:
+            json.dump(allr, f, indent=1)
+        return
     res = compute(a.config, a.scale, a.epochs)
-    allr = load()
-    allr[key(a.config, a.scale)] = res
-    with open(TARGETS, "w") as f:
-        json.dump(allr, f, indent=1)
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(res, f, indent=1)
+    else:
+        allr = load()
+        allr[key(a.config, a.scale)] = res
+        with open(TARGETS, "w") as f:
+            json.dump(allr, f, indent=1)
     print(json.dumps(res))
 
 

@@ -34,6 +34,19 @@
 // position still in flight, no copy is made, and the latest such position
 // writes its updated row into the later position's slot as well.
 //
+// Storage formats (template parameter PR): binary32 W and H; bfloat16 W and
+// H; FP8-E4M3 W with one binary32 scale per row and binary32 H.  Arithmetic
+// is binary32 in every format.  The narrow formats round W stochastically at
+// every update (and bfloat16 H once per visit) with 16 random bits per entry
+// from Philox4x32-10: W of record r in epoch e at counter
+// (r lo, r hi, e, 0x57000000 | chunk/2); H at
+// (segment, e, 0, 0x48000000 | chunk), words z,w; entry 4c+i takes half i%2
+// of word i/2 (word 2 + i/2 for H); one W draw serves two chunks (words x,y
+// for chunk 2q, z,w for chunk 2q+1 at counter word 0x57000000 | q).  The
+// draws do not depend on the updates, so they are made ahead of them in
+// bulk (32 positions of the stream, or a block of a long visit, spread over
+// the lanes as independent draws) and kept in shared memory.
+//
 // The worker body is shared by the one-problem kernel and a form that runs
 // several independent problems in one launch (nomad_batched_many_kernel).
 #include "sgd_common.cuh"
@@ -41,8 +54,8 @@
 namespace nomad {
 namespace {
 
-// Tokens taken from the ring at once: 16 when a row is one 16-byte chunk per
-// lane, 8 otherwise (shared memory holds their h).
+// Tokens taken from the ring at once: 16 when a row is one chunk per lane,
+// 8 otherwise (shared memory holds their h).
 template <int CPL>
 constexpr int Batch = CPL == 1 ? 16 : 8;
 constexpr int kRecBuf = 128;   // circular buffer of record positions
@@ -55,10 +68,13 @@ constexpr int kBatchedWarps = 8;   // warps per thread block at most (register b
 constexpr int kVisitChunks = 21;   // ring chunks of a long visit at one chunk per lane
 constexpr int kUrgentChunks = 14;  // ring chunks of a visit taken out of turn
 
-// Row ring per lane: CHUNKS 16-byte chunks.  The generic stream uses the
-// first kStreamChunks and a long visit of the batch the first VISIT (each
-// runs alone); at one chunk per lane a visit of an urgent item that
-// interrupts either of them uses the kUrgentChunks after those.
+constexpr int kF32 = 0, kBF16 = 1, kFP8 = 2;  // storage formats
+
+// Row ring per lane: CHUNKS chunks.  The generic stream uses the first
+// kStreamChunks and a long visit of the batch the first VISIT (each runs
+// alone); at one chunk per lane a visit of an urgent item that interrupts
+// either of them uses the kUrgentChunks after those.  A row slot is CPL
+// chunks per lane; FP8 rows also keep their scale, one float per slot.
 template <int CPL>
 struct RowRing {
   static constexpr int VISIT = CPL == 1 ? kVisitChunks : kStreamChunks;
@@ -67,28 +83,36 @@ struct RowRing {
   static_assert(kStreamChunks <= VISIT, "the stream's slots lie in the batch's region");
 };
 
-// Storage of W and H: binary32 (a chunk of 4 entries is a float4) or
-// bfloat16 (a chunk is 4 x 16 bits in a uint2).  Arithmetic is binary32 in
-// both cases; bfloat16 rows are widened on load and stochastically rounded on
-// write-back (16 random bits per entry from Philox4x32-10 at counter
-// (record lo, record hi, epoch, 0x57000000 | chunk) for W and
-// (segment, epoch, 0, 0x48000000 | chunk) for H; entry 4c+i takes half i%2 of
-// word i/2, or of word 2 + i/2 for H).
-template <bool BF>
-struct Storage;
+// A chunk is 4 consecutive entries of a row: float4 (binary32), uint2
+// (bfloat16) or uint32_t (four E4M3 codes, entry 4c+i in byte i).
+template <int PR>
+struct Fmt;
 template <>
-struct Storage<false> {
-  using chunk_t = float4;
-  static __device__ __forceinline__ float4 widen(float4 c) { return c; }
+struct Fmt<kF32> {
+  using w_t = float4;
+  using h_t = float4;
 };
 template <>
-struct Storage<true> {
-  using chunk_t = uint2;
-  static __device__ __forceinline__ float4 widen(uint2 c) {
-    return make_float4(__uint_as_float(c.x << 16), __uint_as_float(c.x & 0xffff0000u),
-                       __uint_as_float(c.y << 16), __uint_as_float(c.y & 0xffff0000u));
-  }
+struct Fmt<kBF16> {
+  using w_t = uint2;
+  using h_t = uint2;
 };
+template <>
+struct Fmt<kFP8> {
+  using w_t = uint32_t;
+  using h_t = float4;
+};
+
+__device__ __forceinline__ float4 bf16_widen(uint2 c) {
+  return make_float4(__uint_as_float(c.x << 16), __uint_as_float(c.x & 0xffff0000u),
+                     __uint_as_float(c.y << 16), __uint_as_float(c.y & 0xffff0000u));
+}
+__device__ __forceinline__ float4 widen_h(float4 c) { return c; }
+__device__ __forceinline__ float4 widen_h(uint2 c) { return bf16_widen(c); }
+// a W chunk as binary32 (s: the row's scale, FP8 only)
+__device__ __forceinline__ float4 widen_w(float4 c, float) { return c; }
+__device__ __forceinline__ float4 widen_w(uint2 c, float) { return bf16_widen(c); }
+__device__ __forceinline__ float4 widen_w(uint32_t c, float s) { return e4m3_unpack(c, s); }
 
 // binary32 -> bfloat16 with 16 random bits added to the dropped bits of the
 // magnitude (stochastic rounding); infinities and NaN are truncated.
@@ -102,13 +126,121 @@ __device__ __forceinline__ uint2 pack_sr(float4 v, uint32_t ra, uint32_t rb) {
                     bf16_sr(v.z, rb) | (bf16_sr(v.w, rb >> 16) << 16));
 }
 
-// Shared memory of one warp in bytes: row slots, h of the batch, records
-// (int2) and two int4 tables of batch metadata.
-template <int CPL, bool BF>
+// The rounding bits of chunks 2q and 2q+1 of the W row written by the update
+// of record `rix` in epoch `e`: words x,y and z,w of one draw.
+__device__ __forceinline__ uint4 w_bits_pair(int64_t rix, int e, int q, uint2 seed) {
+  return philox4x32_10(make_uint4(uint32_t(rix), uint32_t(uint64_t(rix) >> 32), uint32_t(e),
+                                  0x57000000u | uint32_t(q)),
+                       seed);
+}
+
+// The draws of `nu` updates, one per (update u, pair of chunks q), spread
+// over the lanes; the bits of chunk c of update u go to buf[u * CPL * 32 + c].
+// rix(u) and e(u) name the record and epoch of update u: lane u holds them
+// (u < nu <= 32).  w / npairs is taken as umulhi(w, m) with
+// m = floor((2^32 - 1) / npairs) + 1, exact for w < 2^16 and npairs <= 64.
+template <int CPL>
+__device__ __forceinline__ void draw_w_bits(uint2* buf, int nu, int64_t rix, int e, int k4,
+                                            uint2 seed, int lane) {
+  const int npairs = (k4 + 1) >> 1;
+  const uint32_t m = 0xffffffffu / uint32_t(npairs) + 1u;
+  const int items = nu * npairs;
+  for (int base = 0; base < items; base += 32) {
+    const int w = base + lane;
+    const int u = int(__umulhi(uint32_t(w), m));
+    const int q = w - u * npairs;
+    const int us = w < items ? u : 0;
+    const int64_t rx = __shfl_sync(kFull, rix, us);
+    const int ex = __shfl_sync(kFull, e, us);
+    if (w < items) {
+      const uint4 d = w_bits_pair(rx, ex, q, seed);
+      uint2* dst = buf + u * CPL * 32 + 2 * q;
+      dst[0] = make_uint2(d.x, d.y);
+      if (2 * q + 1 < k4) dst[1] = make_uint2(d.z, d.w);
+    }
+  }
+}
+
+// h of a visit written back to H (bfloat16: rounded with the bits of
+// segment `seg` in epoch `e`).
+__device__ __forceinline__ void store_h(float4* dst, float4 h, int, int, int, uint2) {
+  __stcg(dst, h);
+}
+__device__ __forceinline__ void store_h(uint2* dst, float4 h, int seg, int e, int idx, uint2 seed) {
+  const uint4 r = philox4x32_10(
+      make_uint4(uint32_t(seg), uint32_t(e), 0u, 0x48000000u | uint32_t(idx)), seed);
+  __stcg(dst, pack_sr(h, r.z, r.w));
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// The stored form of an updated W row (warp-collective: every lane calls,
+// lanes past the row hold zeros).  wn: this lane's chunks; rb: their
+// rounding bits.  FP8: the new scale (the row's largest magnitude / 448) is
+// returned in *scale.
+template <int PR, int CPL>
+__device__ __forceinline__ void narrow_w(const float4 (&wn)[CPL], const uint2 (&rb)[CPL],
+                                         typename Fmt<PR>::w_t (&out)[CPL], float* scale) {
+#pragma unroll
+  for (int cc = 0; cc < CPL; ++cc) {
+    if constexpr (PR == kF32) out[cc] = wn[cc];
+    if constexpr (PR == kBF16) out[cc] = pack_sr(wn[cc], rb[cc].x, rb[cc].y);
+  }
+  if constexpr (PR == kFP8) {
+    float a = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < CPL; ++cc) a = abs_max4(wn[cc], a);
+    a = warp_max(a);
+    float s, g;
+    e4m3_row_scale(a, &s, &g);
+#pragma unroll
+    for (int cc = 0; cc < CPL; ++cc) out[cc] = e4m3_pack(wn[cc], g, true, rb[cc].x, rb[cc].y);
+    *scale = s;
+  }
+}
+
+// Packed binary32 pairs (Blackwell's two-wide FMA): a chunk of 4 entries is
+// handled as two float2 halves.
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+// acc + a.b over the 4 entries, kept as two partial sums
+__device__ __forceinline__ float2 dot4_acc(float4 a, float4 b, float2 acc) {
+  acc = __ffma2_rn(lo2(a), lo2(b), acc);
+  return __ffma2_rn(hi2(a), hi2(b), acc);
+}
+// per entry: fma(b, y, a * x)
+__device__ __forceinline__ float4 axpby(float2 a2, float4 x, float2 b2, float4 y) {
+  return cat4(__ffma2_rn(b2, lo2(y), __fmul2_rn(a2, lo2(x))),
+              __ffma2_rn(b2, hi2(y), __fmul2_rn(a2, hi2(x))));
+}
+
+// Shared memory of one warp.  Offsets in bytes, each a multiple of 16: row
+// slots, their scales (FP8), h of the batch, the rounding bits of the stream
+// and of the batch's long visits (narrow formats: SRB positions of CPL*32
+// chunks), those of an urgent visit, records (int2) and two int4 tables of
+// batch metadata.
+template <int CPL, int PR>
+struct WarpSmem {
+  using F = Fmt<PR>;
+  static constexpr int SRB = 32 / CPL;  // stream positions per bulk draw
+  static constexpr int kRows = 0;
+  static constexpr int kScales = kRows + RowRing<CPL>::CHUNKS * 32 * int(sizeof(typename F::w_t));
+  static constexpr int kH = kScales + (PR == kFP8 ? (RowRing<CPL>::CHUNKS * 4 + 15) / 16 * 16 : 0);
+  static constexpr int kSr = kH + Batch<CPL> * CPL * 32 * int(sizeof(typename F::h_t));
+  static constexpr int kUbits = kSr + (PR == kF32 ? 0 : SRB * CPL * 32 * 8);
+  // an urgent visit's block of rounding bits (one chunk per lane, 7 rows)
+  static constexpr int kRecs = kUbits + (PR == kF32 || CPL != 1 ? 0 : 7 * 32 * 8);
+  static constexpr int kMeta = kRecs + kRecBuf * 8;
+  static constexpr int bytes = kMeta + 2 * Batch<CPL> * 16;
+};
+template <int CPL, int PR>
 __host__ __device__ constexpr int warp_smem_bytes() {
-  return int((RowRing<CPL>::CHUNKS + Batch<CPL> * CPL) * 32 *
-             sizeof(typename Storage<BF>::chunk_t)) +
-         kRecBuf * 8 + 2 * Batch<CPL> * 16;
+  return WarpSmem<CPL, PR>::bytes;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -119,6 +251,16 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_chunk(T* smem, const T* gmem) {
+  if constexpr (sizeof(T) == 16) cp_async16(smem, gmem);
+  else if constexpr (sizeof(T) == 8) cp_async8(smem, gmem);
+  else cp_async4(smem, gmem);
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -126,24 +268,48 @@ __device__ __forceinline__ void cp_wait() {
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Copies the records of stream positions [p0, p0 + count) (count <= 32) into
-// the circular buffer.  Lane r < nb holds the stream offset `soff` and first
-// record `beg` of the rank-r visit (offsets increase with the rank).
+// The visit rank of stream position p: the last rank r < nb whose offset is
+// <= p.  Lane r < nb holds the stream offset `soff` of the rank-r visit
+// (offsets increase with the rank).
 template <int KB>
-__device__ __forceinline__ void load_records(int2* recs, const int2* __restrict__ rec, int soff,
-                                             int64_t beg, int nb, int p0, int count, int lane) {
-  const int p = p0 + lane;
-  int r = 0;  // the visit of position p: the last rank whose offset is <= p
+__device__ __forceinline__ int rank_of(int soff, int nb, int p) {
+  int r = 0;
 #pragma unroll
   for (int i = 1; i < KB; ++i) {
     const int o = __shfl_sync(kFull, soff, i);
     if (i < nb && o <= p) r = i;
   }
+  return r;
+}
+
+// Copies the records of stream positions [p0, p0 + count) (count <= 32) into
+// the circular buffer.  Lane r < nb holds the stream offset `soff` and first
+// record `beg` of the rank-r visit.
+template <int KB>
+__device__ __forceinline__ void load_records(int2* recs, const int2* __restrict__ rec, int soff,
+                                             int64_t beg, int nb, int p0, int count, int lane) {
+  const int p = p0 + lane;
+  const int r = rank_of<KB>(soff, nb, p);
   const int o = __shfl_sync(kFull, soff, r);
   const int64_t b = __shfl_sync(kFull, beg, r);
   if (lane < count) cp_async8(recs + (p % kRecBuf), rec + b + (p - o));
 }
 
+// The rounding bits of stream positions [p0, min(p0 + SRB, T)), all chunks,
+// into srb[(p - p0) * CPL * 32 + chunk].  Lane r < nb holds the offset,
+// first record and epoch of the rank-r visit.
+template <int KB, int CPL>
+__device__ __forceinline__ void draw_stream_bits(uint2* srb, int soff, int64_t beg, int ep, int nb,
+                                                 int p0, int T, int k4, uint2 seed, int lane) {
+  constexpr int SRB = 32 / CPL;
+  const int p = p0 + (lane < SRB ? lane : 0);  // lane u < SRB: position p0 + u
+  const int r = rank_of<KB>(soff, nb, p);
+  const int o = __shfl_sync(kFull, soff, r);
+  const int64_t b = __shfl_sync(kFull, beg, r);
+  const int e = __shfl_sync(kFull, ep, r);
+  const int nu = T - p0 < SRB ? T - p0 : SRB;
+  draw_w_bits<CPL>(srb, nu, b + (p - o), e, k4, seed, lane);
+}
 
 // Transposed warp reduction: v[0..31] are this lane's partial sums of 32
 // quantities; on return lane l holds the warp-wide sum of quantity l.  Each
@@ -182,16 +348,17 @@ __device__ __forceinline__ float warp_sum_transposed(float (&v)[32], int lane) {
 // a full warp reduction to one shuffle and one multiply-add.
 //
 // W rows come through NCH chunk slots per lane of the warp's shared-memory
-// ring (`rows`), LB blocks ahead with cp.async; each lane copies and reads
-// only its own chunk of a row.  Records are held in lane registers,
-// three 32-record chunks (lane i holds record i of a chunk).  Earlier stores
-// of this warp precede these loads in program order.
-template <int CPL, bool BF, bool DEBUG, int NCH>
-__device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF>::chunk_t* rows,
-                                           typename Storage<BF>::chunk_t* W4, int64_t pitch4,
-                                           int k4, const int2* __restrict__ rec, int64_t beg,
-                                           int c, float s, float lam, int epoch, uint2 seed,
-                                           int lane, int32_t* rec_count) {
+// ring (`rows`, with the scale of each row slot in `rsc` for FP8), LB blocks
+// ahead with cp.async; each lane copies and reads only its own chunk of a
+// row.  Records are held in lane registers, three 32-record chunks (lane i
+// holds record i of a chunk).  Earlier stores of this warp precede these
+// loads in program order.
+template <int CPL, int PR, bool DEBUG, int NCH>
+__device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Fmt<PR>::w_t* rows, float* rsc,
+                                           uint2* rbuf, typename Fmt<PR>::w_t* W4, float* Wscale,
+                                           int64_t pitch4, int k4, const int2* __restrict__ rec,
+                                           int64_t beg, int c, float s, float lam, int epoch,
+                                           uint2 seed, int lane, int32_t* rec_count) {
   constexpr int B = CPL == 4 ? 4 : 7;
   constexpr int NS = B + B * (B - 1) / 2;
   static_assert(NS <= 32, "one transposed reduction per block");
@@ -199,7 +366,7 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
   // record chunks c0 and c0 + 1
   constexpr int LB = (NCH / CPL) / B < 33 / B - 1 ? (NCH / CPL) / B : 33 / B - 1;
   static_assert(LB >= 1 && B * (LB + 1) - 1 <= 32, "row ring holds the blocks in flight");
-  using chunk_t = typename Storage<BF>::chunk_t;
+  using w_t = typename Fmt<PR>::w_t;
   const float al = 1.f - s * lam;
   // lane u < B: a^u, and s a^(u-1-v) for v < u
   float aD = 1.f;
@@ -235,12 +402,11 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc) {
           const int idx = lane + 32 * cc;
-          if (idx < k4) {
-            chunk_t* dst = rows + ((set * B + i) * CPL + cc) * 32 + lane;
-            if constexpr (BF) cp_async8(dst, W4 + int64_t(row) * pitch4 + idx);
-            else cp_async16(dst, W4 + int64_t(row) * pitch4 + idx);
-          }
+          if (idx < k4)
+            cp_chunk(rows + ((set * B + i) * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
         }
+        if constexpr (PR == kFP8)
+          if (lane == 0) cp_async4(rsc + set * B + i, Wscale + row);
       }
     }
     cp_commit();
@@ -248,6 +414,7 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
 #pragma unroll
   for (int l = 0; l < LB; ++l) fetch(l);
 
+  const float2 al2 = make_float2(al, al);
   const int nblk = (c + B - 1) / B;
   for (int b = 0; b < nblk; ++b) {
     if (((b * B) >> 5) != c0) {  // next record chunk
@@ -258,44 +425,50 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
       r2 = p2 < c ? __ldcs(rec + beg + p2) : z2;
     }
     cp_wait<LB - 1>();
+    if constexpr (PR == kFP8) __syncwarp();  // lane 0's copies of the scales have landed
     const int set = int(unsigned(b) % unsigned(LB));
     float4 w[B][CPL];
 #pragma unroll
-    for (int i = 0; i < B; ++i)
+    for (int i = 0; i < B; ++i) {
+      const float sc = PR == kFP8 ? rsc[set * B + i] : 1.f;
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc)
         w[i][cc] = lane + 32 * cc < k4 && b * B + i < c
-                       ? Storage<BF>::widen(rows[((set * B + i) * CPL + cc) * 32 + lane])
+                       ? widen_w(rows[((set * B + i) * CPL + cc) * 32 + lane], sc)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if constexpr (PR == kFP8) __syncwarp();  // every lane has read the scales before they are refilled
     // lane partials: slots 0..B-1 <w_u, h_0>, then <w_u, w_v> for v < u
+    // (two-wide FMAs, the halves summed at the end)
     float v[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) v[t] = 0.f;
 #pragma unroll
-    for (int u = 0; u < B; ++u)
+    for (int u = 0; u < B; ++u) {
+      float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int cc = 0; cc < CPL; ++cc) {
-        v[u] = fmaf(w[u][cc].x, h[cc].x, v[u]);
-        v[u] = fmaf(w[u][cc].y, h[cc].y, v[u]);
-        v[u] = fmaf(w[u][cc].z, h[cc].z, v[u]);
-        v[u] = fmaf(w[u][cc].w, h[cc].w, v[u]);
-      }
+      for (int cc = 0; cc < CPL; ++cc) a = dot4_acc(w[u][cc], h[cc], a);
+      v[u] = a.x + a.y;
+    }
 #pragma unroll
     for (int u = 1; u < B; ++u)
 #pragma unroll
       for (int q = 0; q < u; ++q) {
         const int t = B + u * (u - 1) / 2 + q;
+        float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) {
-          v[t] = fmaf(w[u][cc].x, w[q][cc].x, v[t]);
-          v[t] = fmaf(w[u][cc].y, w[q][cc].y, v[t]);
-          v[t] = fmaf(w[u][cc].z, w[q][cc].z, v[t]);
-          v[t] = fmaf(w[u][cc].w, w[q][cc].w, v[t]);
-        }
+        for (int cc = 0; cc < CPL; ++cc) a = dot4_acc(w[u][cc], w[q][cc], a);
+        v[t] = a.x + a.y;
       }
     // the slots just read take the rows of block b + LB (the partials above
     // consumed every value read from them)
     fetch(b + LB);
+    // the block's rounding bits (narrow formats): independent of the
+    // updates, drawn here so that the draws overlap the reduction below
+    if constexpr (PR != kF32) {
+      __syncwarp();  // every lane has read the previous block's bits
+      draw_w_bits<CPL>(rbuf, B, beg + b * B + (lane < B ? lane : 0), epoch, k4, seed, lane);
+    }
     const float red = warp_sum_transposed(v, lane);
     // lane u < B: A_u - a^u <w_u, h_0>, then the forward substitution
     float acc;
@@ -317,6 +490,7 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
       e[q] = __shfl_sync(kFull, acc, q);
       if (q < B - 1 && lane > q) acc = fmaf(-gs[q], e[q], acc);
     }
+    if constexpr (PR != kF32) __syncwarp();  // the bits drawn above are visible
     // vector updates in rating order
     const int nu = c - b * B < B ? c - b * B : B;
 #pragma unroll
@@ -324,51 +498,49 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Storage<BF
       if (i >= nu) break;
       const int u = b * B + i;
       const float se = s * e[i];
-      chunk_t* wrow = W4 + int64_t(row_at(u)) * pitch4;
+      const float2 se2 = make_float2(se, se);
+      const int row = row_at(u);
+      w_t* wrow = W4 + int64_t(row) * pitch4;
+      float4 wn[CPL];
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
-        const int idx = lane + 32 * cc;
-        float4 wn;
-        wn.x = fmaf(se, h[cc].x, al * w[i][cc].x);
-        wn.y = fmaf(se, h[cc].y, al * w[i][cc].y);
-        wn.z = fmaf(se, h[cc].z, al * w[i][cc].z);
-        wn.w = fmaf(se, h[cc].w, al * w[i][cc].w);
-        h[cc].x = fmaf(al, h[cc].x, se * w[i][cc].x);
-        h[cc].y = fmaf(al, h[cc].y, se * w[i][cc].y);
-        h[cc].z = fmaf(al, h[cc].z, se * w[i][cc].z);
-        h[cc].w = fmaf(al, h[cc].w, se * w[i][cc].w);
-        if (idx < k4) {
-          if constexpr (BF) {
-            const int64_t rix = beg + u;
-            const uint4 rb = philox4x32_10(
-                make_uint4(uint32_t(rix), uint32_t(uint64_t(rix) >> 32), uint32_t(epoch),
-                           0x57000000u | uint32_t(idx)),
-                seed);
-            wrow[idx] = pack_sr(wn, rb.x, rb.y);
-          } else {
-            wrow[idx] = wn;
-          }
-        }
+        wn[cc] = axpby(al2, w[i][cc], se2, h[cc]);  // a w_u + s e_u h_u
+        h[cc] = axpby(se2, w[i][cc], al2, h[cc]);   // a h_u + s e_u w_u
       }
+      uint2 rb[CPL];
+      if constexpr (PR != kF32) {
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) rb[cc] = rbuf[i * CPL * 32 + lane + 32 * cc];
+      }
+      w_t out[CPL];
+      float scale = 1.f;
+      narrow_w<PR, CPL>(wn, rb, out, &scale);
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc)
+        if (lane + 32 * cc < k4) wrow[lane + 32 * cc] = out[cc];
+      if constexpr (PR == kFP8)
+        if (lane == 0) Wscale[row] = scale;
       if (DEBUG && lane == 0) rec_count[beg + u] += 1;
     }
   }
   cp_wait<0>();
+  if constexpr (PR == kFP8) __syncwarp();
 }
 
 // A visit of an urgent item's token taken out of turn by worker q (one
-// 16-byte chunk of a row per lane): segment `useg`, just popped from q's
-// ring.  The steps of a long visit of a batch: metadata, h_j into registers,
-// the updates (in the ring slots `rows`, disjoint from those of the
+// chunk of a row per lane): segment `useg`, just popped from q's ring.  The
+// steps of a long visit of a batch: metadata, h_j into registers, the
+// updates (in the ring slots `rows` / `rsc`, disjoint from those of the
 // interrupted work), h_j back to H, the token handed on at once.  Visits are
-// never split: the check runs between visits.  Not inlined: it is reached from
-// two places and runs a few hundred times per worker and epoch.
-template <bool BF, bool DEBUG>
+// never split: the check runs between visits.  Not inlined: it is reached
+// from two places and runs a few hundred times per worker and epoch.
+template <int PR, bool DEBUG>
 __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, uint32_t item,
-                                          typename Storage<BF>::chunk_t* rows) {
-  using chunk_t = typename Storage<BF>::chunk_t;
-  chunk_t* __restrict__ W4 = reinterpret_cast<chunk_t*>(P.W);
-  chunk_t* __restrict__ H4 = reinterpret_cast<chunk_t*>(P.H);
+                                          typename Fmt<PR>::w_t* rows, float* rsc, uint2* rbuf) {
+  using w_t = typename Fmt<PR>::w_t;
+  using h_t = typename Fmt<PR>::h_t;
+  w_t* __restrict__ W4 = reinterpret_cast<w_t*>(P.W);
+  h_t* __restrict__ H4 = reinterpret_cast<h_t*>(P.H);
   const int64_t pitch4 = P.pitch >> 2;
   const int k4 = P.k4;
   const uint2 seed = make_uint2(P.seed_lo, P.seed_hi);
@@ -383,7 +555,7 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
   const int ucb = rb4.y;
   const int ud = rb4.z;
   float4 uh[1];
-  uh[0] = lane < k4 ? Storage<BF>::widen(__ldcg(H4 + int64_t(uj) * pitch4 + lane))
+  uh[0] = lane < k4 ? widen_h(__ldcg(H4 + int64_t(uj) * pitch4 + lane))
                     : make_float4(0.f, 0.f, 0.f, 0.f);
   const float us = __ldg(P.step + (ue - P.epoch0));
   int unh = uhop + 1, une = ue;
@@ -409,17 +581,9 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
     }
     if (atomicExch(P.owner + uj, q) != -1) flag_ownership(P, q, uj);
   }
-  long_visit<1, BF, DEBUG, kUrgentChunks>(uh, rows, W4, pitch4, k4, P.rec, ubeg, uc, us,
-                                         P.lambda, ue, seed, lane, P.rec_count);
-  if (lane < k4) {
-    if constexpr (BF) {
-      const uint4 rb = philox4x32_10(
-          make_uint4(useg, uint32_t(ue), 0u, 0x48000000u | uint32_t(lane)), seed);
-      __stcg(H4 + int64_t(uj) * pitch4 + lane, pack_sr(uh[0], rb.z, rb.w));
-    } else {
-      __stcg(H4 + int64_t(uj) * pitch4 + lane, uh[0]);
-    }
-  }
+  long_visit<1, PR, DEBUG, kUrgentChunks>(uh, rows, rsc, rbuf, W4, P.Wscale, pitch4, k4, P.rec,
+                                          ubeg, uc, us, P.lambda, ue, seed, lane, P.rec_count);
+  if (lane < k4) store_h(H4 + int64_t(uj) * pitch4 + lane, uh[0], int(useg), ue, lane, seed);
   if (lane == 0) {
     if (unseg >= 0) {
       __stcg(P.tok_rec + 2 * uj, make_int4(unseg, unc, int(uint32_t(unbeg)), une));
@@ -432,26 +596,33 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
 }
 
 // Worker q of the problem P (one warp), with its shared memory at `wsmem`
-// (warp_smem_bytes<CPL, BF>() bytes).
-template <int CPL, bool BF, bool DEBUG>
+// (warp_smem_bytes<CPL, PR>() bytes).
+template <int CPL, int PR, bool DEBUG>
 __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsigned char* wsmem) {
   constexpr int R = RowRing<CPL>::R;
-  using chunk_t = typename Storage<BF>::chunk_t;
+  using SM = WarpSmem<CPL, PR>;
+  using w_t = typename Fmt<PR>::w_t;
+  using h_t = typename Fmt<PR>::h_t;
+  constexpr int SRB = SM::SRB;
   const int lane = threadIdx.x & 31;
-  chunk_t* rows = reinterpret_cast<chunk_t*>(wsmem);
-  chunk_t* hbuf = rows + RowRing<CPL>::CHUNKS * 32;
+  w_t* rows = reinterpret_cast<w_t*>(wsmem + SM::kRows);
+  float* rsc = reinterpret_cast<float*>(wsmem + SM::kScales);  // FP8: scale of each row slot
+  h_t* hbuf = reinterpret_cast<h_t*>(wsmem + SM::kH);
+  uint2* srb = reinterpret_cast<uint2*>(wsmem + SM::kSr);      // narrow formats: stream draws
+  uint2* ubits = reinterpret_cast<uint2*>(wsmem + SM::kUbits);  // and an urgent visit's
   constexpr int kBatch = Batch<CPL>;
-  int2* recs = reinterpret_cast<int2*>(hbuf + kBatch * CPL * 32);
-  int4* meta_a = reinterpret_cast<int4*>(recs + kRecBuf);  // {j, c, e, seg}
-  int4* meta_b = meta_a + kBatch;                          // {beg_lo, beg_hi, lane, soff}
+  int2* recs = reinterpret_cast<int2*>(wsmem + SM::kRecs);
+  int4* meta_a = reinterpret_cast<int4*>(wsmem + SM::kMeta);  // {j, c, e, seg}
+  int4* meta_b = meta_a + kBatch;                             // {beg_lo, beg_hi, lane, soff}
 
   const int64_t quota = int64_t(P.worker_seg_ptr[q + 1] - P.worker_seg_ptr[q]) * P.n_epochs;
   if (lane == 0) atomicMin(P.span, globaltimer_ns());  // the launch's time span on the device
   const int lg = P.ring_log2[q];
   const uint32_t qmask = (1u << lg) - 1u;
   const unsigned long long* ring_q = P.ring + P.ring_base[q];
-  chunk_t* __restrict__ W4 = reinterpret_cast<chunk_t*>(P.W);
-  chunk_t* __restrict__ H4 = reinterpret_cast<chunk_t*>(P.H);
+  w_t* __restrict__ W4 = reinterpret_cast<w_t*>(P.W);
+  h_t* __restrict__ H4 = reinterpret_cast<h_t*>(P.H);
+  float* __restrict__ Wscale = P.Wscale;
   const int64_t pitch4 = P.pitch >> 2;
   const int k4 = P.k4;
   const float lam = P.lambda;
@@ -498,7 +669,7 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       useg = __shfl_sync(kFull, useg, 0);
       ++head_u;
       ++done;
-      urgent_visit<BF, DEBUG>(P, q, lane, useg, rows + kVisitChunks * 32);
+      urgent_visit<PR, DEBUG>(P, q, lane, useg, rows + kVisitChunks * 32, rsc + kVisitChunks, ubits);
       return true;
     }
   };
@@ -525,7 +696,7 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       const uint32_t item = uint32_t(__shfl_sync(kFull, sv, 31));
       ++head_u;
       ++done;
-      urgent_visit<BF, DEBUG>(P, q, lane, item, rows + kVisitChunks * 32);
+      urgent_visit<PR, DEBUG>(P, q, lane, item, rows + kVisitChunks * 32, rsc + kVisitChunks, ubits);
       continue;
     }
     unsigned tmask = rmask & ((1u << kRingWindow) - 1u);
@@ -574,7 +745,7 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
     int rank = 0;
     if (mine) rank = ((hv >> lane) & 1u) ? __popc(hv & below) : __popc(hv) + __popc(lt & below);
     if (mine) {
-      meta_a[rank] = make_int4(j, c, 0, seg);
+      meta_a[rank] = make_int4(j, c, e, seg);
       meta_b[rank] = make_int4(int(uint32_t(beg)), int(uint32_t(uint64_t(beg) >> 32)), lane, 0);
     }
     __syncwarp();
@@ -598,18 +769,17 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
-        if (idx < k4) {
-          if constexpr (BF) cp_async8(hbuf + (r * CPL + cc) * 32 + lane, H4 + jr * pitch4 + idx);
-          else cp_async16(hbuf + (r * CPL + cc) * 32 + lane, H4 + jr * pitch4 + idx);
-        }
+        if (idx < k4) cp_chunk(hbuf + (r * CPL + cc) * 32 + lane, H4 + jr * pitch4 + idx);
       }
     }
-    int v_soff = 0;  // lane r < nb: stream offset and first record of the rank-r visit
+    // lane r < nb: stream offset, first record and epoch of the rank-r visit
+    int v_soff = 0, v_ep = 0;
     int64_t v_beg = 0;
     if (lane < nb) {
       const int4 mb = meta_b[lane];
       v_soff = mb.w;
       v_beg = (int64_t(mb.y) << 32) | uint32_t(mb.x);
+      v_ep = meta_a[lane].z;
     }
     // long visits (ranks 0 .. nhv-1) take stream positions [0, T0) and run
     // first on their own path; the generic stream starts at T0
@@ -640,9 +810,6 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
         nseg = __ldg(P.col_segs + cb + itinerary_slot(uint32_t(nh), uint32_t(d), key));
       }
     }
-    if (mine) {
-      meta_a[rank].z = e;
-    }
     cp_wait_all();
     __syncwarp();
     int q2 = -1, nc = 0;  // the next visit: worker, length, first record
@@ -672,7 +839,7 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       float4 hh[CPL];
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc)
-        hh[cc] = lane + 32 * cc < k4 ? Storage<BF>::widen(hbuf[(kh * CPL + cc) * 32 + lane])
+        hh[cc] = lane + 32 * cc < k4 ? widen_h(hbuf[(kh * CPL + cc) * 32 + lane])
                                      : make_float4(0.f, 0.f, 0.f, 0.f);
       if (DEBUG && lane == 0) {
         const uint32_t tk = atomicAdd(P.log_ticket, 1u);
@@ -682,20 +849,13 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
         }
         if (atomicExch(P.owner + ma.x, q) != -1) flag_ownership(P, q, ma.x);
       }
-      long_visit<CPL, BF, DEBUG, RowRing<CPL>::VISIT>(hh, rows, W4, pitch4, k4, P.rec, vb, ma.y,
-                                                      sv, lam, ma.z, seed, lane, P.rec_count);
+      long_visit<CPL, PR, DEBUG, RowRing<CPL>::VISIT>(hh, rows, rsc, srb, W4, Wscale, pitch4, k4,
+                                                      P.rec, vb, ma.y, sv, lam, ma.z, seed, lane,
+                                                      P.rec_count);
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
-        if (idx < k4) {
-          if constexpr (BF) {
-            const uint4 rb = philox4x32_10(
-                make_uint4(uint32_t(ma.w), uint32_t(ma.z), 0u, 0x48000000u | uint32_t(idx)), seed);
-            __stcg(H4 + int64_t(ma.x) * pitch4 + idx, pack_sr(hh[cc], rb.z, rb.w));
-          } else {
-            __stcg(H4 + int64_t(ma.x) * pitch4 + idx, hh[cc]);
-          }
-        }
+        if (idx < k4) store_h(H4 + int64_t(ma.x) * pitch4 + idx, hh[cc], ma.w, ma.z, idx, seed);
       }
       if (lane == vl) {
         write_record();
@@ -715,11 +875,11 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
-        if (idx < k4) {
-          if constexpr (BF) cp_async8(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
-          else cp_async16(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
-        }
+        if (idx < k4)
+          cp_chunk(rows + (slot * CPL + cc) * 32 + lane, W4 + int64_t(row) * pitch4 + idx);
       }
+      if constexpr (PR == kFP8)
+        if (lane == 0) cp_async4(rsc + slot, Wscale + row);
     };
     auto prefetch = [&](int pp, int row) {
       const int slot = pp % R;
@@ -745,9 +905,11 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
     }
 
     // ---- 5b. the stream
-    int k = nhv - 1, vend = T0, vsoff = 0, vlane = 0, vseg = 0;
+    int k = nhv - 1, vend = T0, vsoff = 0, vlane = 0, vseg = 0, vep = 0;
     int64_t vbeg = 0;
     float s = 0.f;
+    float2 al2 = make_float2(1.f, 1.f);
+    int sr_lo = T0, sr_hi = T0;  // stream positions whose rounding bits are in srb
     float4 h[CPL];
 #pragma unroll
     for (int cc = 0; cc < CPL; ++cc) h[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -772,12 +934,14 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
         vsoff = t;
         vend = t + ma.y;
         vseg = ma.w;
+        vep = ma.z;
         vlane = mb.z;
         vbeg = (int64_t(mb.y) << 32) | uint32_t(mb.x);
         s = __shfl_sync(kFull, s_tok, vlane);
+        al2 = make_float2(1.f - s * lam, 1.f - s * lam);
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc)  // lanes past k/4 hold zeros, never smem
-          h[cc] = lane + 32 * cc < k4 ? Storage<BF>::widen(hbuf[(k * CPL + cc) * 32 + lane])
+          h[cc] = lane + 32 * cc < k4 ? widen_h(hbuf[(k * CPL + cc) * 32 + lane])
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
         if (DEBUG && lane == 0) {
           const uint32_t tk = atomicAdd(P.log_ticket, 1u);
@@ -786,6 +950,14 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
             P.log_epoch[tk] = ma.z;
           }
           if (atomicExch(P.owner + ma.x, q) != -1) flag_ownership(P, q, ma.x);
+        }
+      }
+      if constexpr (PR != kF32) {
+        if (t == sr_hi) {  // the next SRB positions' rounding bits, drawn in bulk
+          __syncwarp();    // every lane has read the previous draws
+          draw_stream_bits<kBatch, CPL>(srb, v_soff, v_beg, v_ep, nb, t, T, k4, seed, lane);
+          sr_lo = t;
+          sr_hi = t + SRB;
         }
       }
       // keep the records one chunk ahead of the row prefetch
@@ -808,50 +980,47 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       const int2 rc = recs[t % kRecBuf];
       const int slot = t % R;
       const int fslot = __shfl_sync(kFull, fwd, slot);  // a later position's slot, or -1
-      chunk_t* wrow = W4 + int64_t(rc.x) * pitch4;
+      w_t* wrow = W4 + int64_t(rc.x) * pitch4;
+      const float sc = PR == kFP8 ? rsc[slot] : 1.f;
       float4 w[CPL];
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
         w[cc] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < k4) w[cc] = Storage<BF>::widen(rows[(slot * CPL + cc) * 32 + lane]);
+        if (idx < k4) w[cc] = widen_w(rows[(slot * CPL + cc) * 32 + lane], sc);
       }
-      float part = 0.f;
+      uint2 rb[CPL];
+      if constexpr (PR != kF32) {
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) rb[cc] = srb[(t - sr_lo) * CPL * 32 + lane + 32 * cc];
+      }
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) acc = dot4_acc(w[cc], h[cc], acc);
+      const float err = __int_as_float(rc.y) - warp_sum(acc.x + acc.y);
+      const float se = s * err;
+      const float2 se2 = make_float2(se, se);
+      float4 wn[CPL];
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
-        part = fmaf(w[cc].x, h[cc].x, part);
-        part = fmaf(w[cc].y, h[cc].y, part);
-        part = fmaf(w[cc].z, h[cc].z, part);
-        part = fmaf(w[cc].w, h[cc].w, part);
+        wn[cc] = axpby(al2, w[cc], se2, h[cc]);  // (1 - s lam) w + s e h
+        h[cc] = axpby(se2, w[cc], al2, h[cc]);   // (1 - s lam) h + s e w
       }
-      const float err = __int_as_float(rc.y) - warp_sum(part);
+      w_t out[CPL];
+      float nscale = 1.f;
+      narrow_w<PR, CPL>(wn, rb, out, &nscale);
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
-        float4 wn, hn;
-        wn.x = fmaf(s, fmaf(err, h[cc].x, -lam * w[cc].x), w[cc].x);
-        wn.y = fmaf(s, fmaf(err, h[cc].y, -lam * w[cc].y), w[cc].y);
-        wn.z = fmaf(s, fmaf(err, h[cc].z, -lam * w[cc].z), w[cc].z);
-        wn.w = fmaf(s, fmaf(err, h[cc].w, -lam * w[cc].w), w[cc].w);
-        hn.x = fmaf(s, fmaf(err, w[cc].x, -lam * h[cc].x), h[cc].x);
-        hn.y = fmaf(s, fmaf(err, w[cc].y, -lam * h[cc].y), h[cc].y);
-        hn.z = fmaf(s, fmaf(err, w[cc].z, -lam * h[cc].z), h[cc].z);
-        hn.w = fmaf(s, fmaf(err, w[cc].w, -lam * h[cc].w), h[cc].w);
         if (idx < k4) {
-          chunk_t out;
-          if constexpr (BF) {
-            const int64_t rix = vbeg + (t - vsoff);
-            const uint4 rb = philox4x32_10(
-                make_uint4(uint32_t(rix), uint32_t(uint64_t(rix) >> 32), uint32_t(meta_a[k].z),
-                           0x57000000u | uint32_t(idx)),
-                seed);
-            out = pack_sr(wn, rb.x, rb.y);
-          } else {
-            out = wn;
-          }
-          wrow[idx] = out;
-          if (fslot >= 0) rows[(fslot * CPL + cc) * 32 + lane] = out;
-          h[cc] = hn;
+          wrow[idx] = out[cc];
+          if (fslot >= 0) rows[(fslot * CPL + cc) * 32 + lane] = out[cc];
+        }
+      }
+      if constexpr (PR == kFP8) {
+        if (lane == 0) {
+          Wscale[rc.x] = nscale;
+          if (fslot >= 0) rsc[fslot] = nscale;
         }
       }
       if (DEBUG && lane == 0) P.rec_count[vbeg + (t - vsoff)] += 1;
@@ -862,16 +1031,7 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc) {
           const int idx = lane + 32 * cc;
-          if (idx < k4) {
-            if constexpr (BF) {
-              const uint4 rb = philox4x32_10(
-                  make_uint4(uint32_t(vseg), uint32_t(meta_a[k].z), 0u, 0x48000000u | uint32_t(idx)),
-                  seed);
-              __stcg(H4 + int64_t(jv) * pitch4 + idx, pack_sr(h[cc], rb.z, rb.w));
-            } else {
-              __stcg(H4 + int64_t(jv) * pitch4 + idx, h[cc]);
-            }
-          }
+          if (idx < k4) store_h(H4 + int64_t(jv) * pitch4 + idx, h[cc], vseg, vep, idx, seed);
         }
       }
     }
@@ -888,15 +1048,15 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
   if (lane == 0) atomicMax(P.span + 1, globaltimer_ns());
 }
 
-template <int CPL, bool BF, bool DEBUG>
+template <int CPL, int PR, bool DEBUG>
 __global__ void __launch_bounds__(kBatchedWarps * 32, 1)
 nomad_batched_kernel(const __grid_constant__ SgdParams P) {
   extern __shared__ float4 smem_f4[];
   const int wib = threadIdx.x >> 5;
   const int q = blockIdx.x * (blockDim.x >> 5) + wib;
   if (q >= P.p) return;
-  batched_worker<CPL, BF, DEBUG>(P, q, reinterpret_cast<unsigned char*>(smem_f4) +
-                                           size_t(wib) * warp_smem_bytes<CPL, BF>());
+  batched_worker<CPL, PR, DEBUG>(P, q, reinterpret_cast<unsigned char*>(smem_f4) +
+                                           size_t(wib) * warp_smem_bytes<CPL, PR>());
 }
 
 // Several independent problems in one launch: block b runs block
@@ -904,13 +1064,13 @@ nomad_batched_kernel(const __grid_constant__ SgdParams P) {
 // are copied into shared memory after the warps' areas.  Every block of a
 // problem is resident with the others (cooperative launch), as in the
 // one-problem kernel; problems share nothing.
-template <int CPL, bool BF, bool DEBUG>
+template <int CPL, int PR, bool DEBUG>
 __global__ void __launch_bounds__(kBatchedWarps * 32, 1)
 nomad_batched_many_kernel(const SgdParams* __restrict__ Ps, const int2* __restrict__ blocks) {
   extern __shared__ float4 smem_f4[];
   const int nw = blockDim.x >> 5;
   unsigned char* base = reinterpret_cast<unsigned char*>(smem_f4);
-  SgdParams* Pb = reinterpret_cast<SgdParams*>(base + size_t(nw) * warp_smem_bytes<CPL, BF>());
+  SgdParams* Pb = reinterpret_cast<SgdParams*>(base + size_t(nw) * warp_smem_bytes<CPL, PR>());
   const int2 bp = blocks[blockIdx.x];
   const int* src = reinterpret_cast<const int*>(Ps + bp.x);
   int* dst = reinterpret_cast<int*>(Pb);
@@ -920,17 +1080,24 @@ nomad_batched_many_kernel(const SgdParams* __restrict__ Ps, const int2* __restri
   const int wib = threadIdx.x >> 5;
   const int q = bp.y * nw + wib;
   if (q >= Pb->p) return;
-  batched_worker<CPL, BF, DEBUG>(*Pb, q, base + size_t(wib) * warp_smem_bytes<CPL, BF>());
+  batched_worker<CPL, PR, DEBUG>(*Pb, q, base + size_t(wib) * warp_smem_bytes<CPL, PR>());
 }
 
-template <int CPL, bool BF>
+template <int CPL, int PR>
 const void* batched_ptr(bool debug, bool many, size_t* smem_per_warp) {
-  *smem_per_warp = size_t(warp_smem_bytes<CPL, BF>());
+  *smem_per_warp = size_t(warp_smem_bytes<CPL, PR>());
   if (many)
-    return debug ? (const void*)nomad_batched_many_kernel<CPL, BF, true>
-                 : (const void*)nomad_batched_many_kernel<CPL, BF, false>;
-  return debug ? (const void*)nomad_batched_kernel<CPL, BF, true>
-               : (const void*)nomad_batched_kernel<CPL, BF, false>;
+    return debug ? (const void*)nomad_batched_many_kernel<CPL, PR, true>
+                 : (const void*)nomad_batched_many_kernel<CPL, PR, false>;
+  return debug ? (const void*)nomad_batched_kernel<CPL, PR, true>
+               : (const void*)nomad_batched_kernel<CPL, PR, false>;
+}
+
+template <int CPL>
+const void* batched_ptr_prec(int precision, bool debug, bool many, size_t* smem_per_warp) {
+  if (precision == NOMAD_BF16) return batched_ptr<CPL, kBF16>(debug, many, smem_per_warp);
+  if (precision == NOMAD_FP8) return batched_ptr<CPL, kFP8>(debug, many, smem_per_warp);
+  return batched_ptr<CPL, kF32>(debug, many, smem_per_warp);
 }
 
 }  // namespace
@@ -938,13 +1105,10 @@ const void* batched_ptr(bool debug, bool many, size_t* smem_per_warp) {
 // Kernel pointer and per-warp shared memory (bytes) of the batched kernel,
 // or of its several-problem form (`many`, which also takes sizeof(SgdParams)
 // bytes per block).
-const void* batched_kernel(int k4, bool debug, bool bf16, bool many, size_t* smem_per_warp) {
-  if (k4 <= 32) return bf16 ? batched_ptr<1, true>(debug, many, smem_per_warp)
-                            : batched_ptr<1, false>(debug, many, smem_per_warp);
-  if (k4 <= 64) return bf16 ? batched_ptr<2, true>(debug, many, smem_per_warp)
-                            : batched_ptr<2, false>(debug, many, smem_per_warp);
-  if (k4 <= 128) return bf16 ? batched_ptr<4, true>(debug, many, smem_per_warp)
-                             : batched_ptr<4, false>(debug, many, smem_per_warp);
+const void* batched_kernel(int k4, bool debug, int precision, bool many, size_t* smem_per_warp) {
+  if (k4 <= 32) return batched_ptr_prec<1>(precision, debug, many, smem_per_warp);
+  if (k4 <= 64) return batched_ptr_prec<2>(precision, debug, many, smem_per_warp);
+  if (k4 <= 128) return batched_ptr_prec<4>(precision, debug, many, smem_per_warp);
   return nullptr;
 }
 

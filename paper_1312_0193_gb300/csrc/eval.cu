@@ -1,7 +1,8 @@
 // eval.cu -- factor initialisation, test RMSE, objective and factor copies.
 //
 // Initialisation (Alg. 1; Sec. 5.1): every entry of W and H is an
-// independent UniformReal(0, 1/sqrt(k)).  Entry (r, l) of factor f (0 = W,
+// independent UniformReal(0, 1/sqrt(k)) (in E4M3 storage of W: those values
+// rounded to nearest with each row's scale).  Entry (r, l) of factor f (0 = W,
 // 1 = H) takes word (l mod 4) of Philox4x32-10(key = seed, counter =
 // (l/4, r_lo, r_hi, f)); u = (word >> 8) 2^-24 and the entry is the binary32
 // product u * c, c = binary32(1/sqrt k) computed on the host.
@@ -32,6 +33,13 @@ __device__ __forceinline__ float4 widen4(uint2 c) {
                      __uint_as_float(c.y << 16), __uint_as_float(c.y & 0xffff0000u));
 }
 __device__ __forceinline__ float4 widen4(float4 c) { return c; }
+// a chunk of W as binary32: binary32 / bfloat16 chunks, or four E4M3 codes
+// times the row's scale
+__device__ __forceinline__ float4 widen_w4(float4 c, const float*, int64_t) { return c; }
+__device__ __forceinline__ float4 widen_w4(uint2 c, const float*, int64_t) { return widen4(c); }
+__device__ __forceinline__ float4 widen_w4(uint32_t c, const float* scale, int64_t row) {
+  return e4m3_unpack(c, scale[row]);
+}
 __device__ __forceinline__ uint2 narrow4(float4 v) {
   return make_uint2(bf16_rn(v.x) | (bf16_rn(v.y) << 16), bf16_rn(v.z) | (bf16_rn(v.w) << 16));
 }
@@ -61,6 +69,91 @@ __global__ void init_factor_kernel(C* __restrict__ F, int64_t rows, int32_t k,
   }
 }
 
+// Initial W in E4M3 storage: the binary32 values of init_factor_kernel,
+// then per row the scale (largest magnitude / 448) and codes rounded to
+// nearest.  One warp per row, lane l holds chunks l, l + 32, ...
+__global__ void init_w_e4m3_kernel(uint32_t* __restrict__ codes, float* __restrict__ scales,
+                                   int64_t rows, int32_t k, int32_t k4, int64_t pitch4, float c,
+                                   uint2 seed) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows; r += nwarps) {
+    float4 v[4];
+    float a = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ch = lane + 32 * i;
+      v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ch < k4) {
+        const uint4 w = philox4x32_10(
+            make_uint4(uint32_t(ch), uint32_t(r), uint32_t(uint64_t(r) >> 32), kTagInitW), seed);
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+        float x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float u = float(words[j] >> 8) * (1.0f / 16777216.0f);  // exact
+          x[j] = (4 * ch + j < k) ? __fmul_rn(u, c) : 0.0f;
+        }
+        v[i] = make_float4(x[0], x[1], x[2], x[3]);
+      }
+      a = abs_max4(v[i], a);
+    }
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(kFull, a, o));
+    float sc, g;
+    e4m3_row_scale(a, &sc, &g);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ch = lane + 32 * i;
+      if (ch < k4) codes[r * pitch4 + ch] = e4m3_pack(v[i], g, false, 0u, 0u);
+    }
+    if (lane == 0) scales[r] = sc;
+  }
+}
+
+// Dense binary32 rows (k entries each) into E4M3 codes and scales, rounded
+// to nearest; one warp per row.
+__global__ void f32_rows_to_e4m3(const float* __restrict__ src, int64_t rows, int32_t k,
+                                 int32_t k4, int64_t pitch4, uint32_t* __restrict__ codes,
+                                 float* __restrict__ scales) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows; r += nwarps) {
+    float4 v[4];
+    float a = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ch = lane + 32 * i;
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      if (ch < k4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * ch + j < k) x[j] = src[r * k + 4 * ch + j];
+      }
+      v[i] = make_float4(x[0], x[1], x[2], x[3]);
+      a = abs_max4(v[i], a);
+    }
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(kFull, a, o));
+    float sc, g;
+    e4m3_row_scale(a, &sc, &g);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ch = lane + 32 * i;
+      if (ch < k4) codes[r * pitch4 + ch] = e4m3_pack(v[i], g, false, 0u, 0u);
+    }
+    if (lane == 0) scales[r] = sc;
+  }
+}
+
+__global__ void e4m3_rows_to_f32(const uint8_t* __restrict__ codes, const float* __restrict__ scales,
+                                 int64_t rows, int32_t k, int32_t pitch, float* __restrict__ dst) {
+  const int64_t total = rows * k;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int64_t r = t / k, l = t - r * k;
+    dst[t] = __fmul_rn(scales[r], e4m3_value(codes[r * pitch + l]));
+  }
+}
+
 // Group of G lanes per rating (G = power of two >= number of 4-entry chunks,
 // at most 32); each warp handles 32/G ratings at a time.
 __device__ __forceinline__ float group_sum(float v, int G) {
@@ -81,9 +174,10 @@ __device__ __forceinline__ void block_store_sum(double acc, double* __restrict__
   }
 }
 
-template <typename C>
+template <typename CW, typename CH>
 __global__ void __launch_bounds__(kEvalThreads)
-sq_error_kernel(const C* __restrict__ W4, const C* __restrict__ H4,
+sq_error_kernel(const CW* __restrict__ W4, const float* __restrict__ Wscale,
+                const CH* __restrict__ H4,
                 int64_t pitch4, int32_t k4, int32_t G, const int32_t* __restrict__ rows,
                 const int32_t* __restrict__ cols, const float* __restrict__ vals,
                 int64_t nnz, int64_t m, int64_t n, int32_t* __restrict__ status,
@@ -106,7 +200,7 @@ sq_error_kernel(const C* __restrict__ W4, const C* __restrict__ H4,
     }
     float part = 0.f;
     for (int ch = sub; ch < k4; ch += G) {
-      const float4 w = widen4(W4[i * pitch4 + ch]), h = widen4(H4[j * pitch4 + ch]);
+      const float4 w = widen_w4(W4[i * pitch4 + ch], Wscale, i), h = widen4(H4[j * pitch4 + ch]);
       part = fmaf(w.x, h.x, part);
       part = fmaf(w.y, h.y, part);
       part = fmaf(w.z, h.z, part);
@@ -123,9 +217,10 @@ sq_error_kernel(const C* __restrict__ W4, const C* __restrict__ H4,
 
 // J over the loaded training ratings, visiting segment by segment so that
 // h_j of the segment's item is known.
-template <typename C>
+template <typename CW, typename CH>
 __global__ void __launch_bounds__(kEvalThreads)
-objective_kernel(const C* __restrict__ W4, const C* __restrict__ H4,
+objective_kernel(const CW* __restrict__ W4, const float* __restrict__ Wscale,
+                 const CH* __restrict__ H4,
                  int64_t pitch4, int32_t k4, const int2* __restrict__ rec,
                  const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_col,
                  int64_t n_seg, float lambda, double* __restrict__ partials) {
@@ -146,7 +241,8 @@ objective_kernel(const C* __restrict__ W4, const C* __restrict__ H4,
       const int64_t i = rc.x;
       float dot = 0.f, ww = 0.f;
       for (int ch = lane; ch < k4; ch += 32) {
-        const float4 w = widen4(W4[i * pitch4 + ch]), h = widen4(H4[j * pitch4 + ch]);
+        const float4 w = widen_w4(W4[i * pitch4 + ch], Wscale, i),
+                     h = widen4(H4[j * pitch4 + ch]);
         dot = fmaf(w.x, h.x, fmaf(w.y, h.y, fmaf(w.z, h.z, fmaf(w.w, h.w, dot))));
         ww = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, ww))));
       }
@@ -218,7 +314,12 @@ int init_factors(nomad_handle* h, cudaStream_t st) {
   const uint2 seed = make_uint2(uint32_t(h->sched.seed), uint32_t(h->sched.seed >> 32));
   const int64_t pitch4 = h->pitch / 4;
   const int grid = eval_grid(h);
-  if (h->elem == 2) {
+  if (h->w_elem == 1) {
+    init_w_e4m3_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<uint32_t*>(h->W), h->Wscale,
+                                                     h->m, h->k, h->k4, pitch4, c, seed);
+    init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<float4*>(h->H), h->n, h->k,
+                                                     h->k4, pitch4, c, kTagInitH, seed);
+  } else if (h->elem == 2) {
     init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<uint2*>(h->W), h->m, h->k,
                                                      h->k4, pitch4, c, kTagInitW, seed);
     init_factor_kernel<<<grid, kEvalThreads, 0, st>>>(static_cast<uint2*>(h->H), h->n, h->k,
@@ -239,14 +340,18 @@ int rmse_sum(nomad_handle* h, int64_t nnz, const int32_t* d_rows, const int32_t*
   if (int rc = ensure_partials(h, grid)) return rc;
   int G = 1;
   while (G < h->k4 && G < 32) G <<= 1;
-  if (h->elem == 2)
+  if (h->w_elem == 1)
     sq_error_kernel<<<grid, kEvalThreads, 0, st>>>(
-        static_cast<const uint2*>(h->W), static_cast<const uint2*>(h->H), h->pitch / 4, h->k4,
-        G, d_rows, d_cols, d_vals, nnz, h->m, h->n, h->status, h->partials);
+        static_cast<const uint32_t*>(h->W), h->Wscale, static_cast<const float4*>(h->H),
+        h->pitch / 4, h->k4, G, d_rows, d_cols, d_vals, nnz, h->m, h->n, h->status, h->partials);
+  else if (h->elem == 2)
+    sq_error_kernel<<<grid, kEvalThreads, 0, st>>>(
+        static_cast<const uint2*>(h->W), nullptr, static_cast<const uint2*>(h->H), h->pitch / 4,
+        h->k4, G, d_rows, d_cols, d_vals, nnz, h->m, h->n, h->status, h->partials);
   else
     sq_error_kernel<<<grid, kEvalThreads, 0, st>>>(
-        static_cast<const float4*>(h->W), static_cast<const float4*>(h->H), h->pitch / 4, h->k4,
-        G, d_rows, d_cols, d_vals, nnz, h->m, h->n, h->status, h->partials);
+        static_cast<const float4*>(h->W), nullptr, static_cast<const float4*>(h->H), h->pitch / 4,
+        h->k4, G, d_rows, d_cols, d_vals, nnz, h->m, h->n, h->status, h->partials);
   sum_partials<<<1, 256, 0, st>>>(h->partials, grid, h->result);
   h->launches += 2;
   if (cudaMemcpyAsync(out, h->result, sizeof(double), cudaMemcpyDeviceToHost, st) !=
@@ -258,14 +363,18 @@ int rmse_sum(nomad_handle* h, int64_t nnz, const int32_t* d_rows, const int32_t*
 int objective_sum(nomad_handle* h, double* out, cudaStream_t st) {
   const int grid = eval_grid(h);
   if (int rc = ensure_partials(h, grid)) return rc;
-  if (h->elem == 2)
+  if (h->w_elem == 1)
     objective_kernel<<<grid, kEvalThreads, 0, st>>>(
-        static_cast<const uint2*>(h->W), static_cast<const uint2*>(h->H), h->pitch / 4, h->k4,
-        h->rec, h->seg_ptr, h->seg_col, h->n_seg, h->lambda, h->partials);
+        static_cast<const uint32_t*>(h->W), h->Wscale, static_cast<const float4*>(h->H),
+        h->pitch / 4, h->k4, h->rec, h->seg_ptr, h->seg_col, h->n_seg, h->lambda, h->partials);
+  else if (h->elem == 2)
+    objective_kernel<<<grid, kEvalThreads, 0, st>>>(
+        static_cast<const uint2*>(h->W), nullptr, static_cast<const uint2*>(h->H), h->pitch / 4,
+        h->k4, h->rec, h->seg_ptr, h->seg_col, h->n_seg, h->lambda, h->partials);
   else
     objective_kernel<<<grid, kEvalThreads, 0, st>>>(
-        static_cast<const float4*>(h->W), static_cast<const float4*>(h->H), h->pitch / 4, h->k4,
-        h->rec, h->seg_ptr, h->seg_col, h->n_seg, h->lambda, h->partials);
+        static_cast<const float4*>(h->W), nullptr, static_cast<const float4*>(h->H), h->pitch / 4,
+        h->k4, h->rec, h->seg_ptr, h->seg_col, h->n_seg, h->lambda, h->partials);
   sum_partials<<<1, 256, 0, st>>>(h->partials, grid, h->result);
   h->launches += 2;
   if (cudaMemcpyAsync(out, h->result, sizeof(double), cudaMemcpyDeviceToHost, st) !=
@@ -277,6 +386,13 @@ int objective_sum(nomad_handle* h, double* out, cudaStream_t st) {
 int factors_to_f32(nomad_handle* h, int which, float* d_dense, cudaStream_t st) {
   const int64_t rows = which == 0 ? h->m : h->n;
   const void* src = which == 0 ? h->W : h->H;
+  if (which == 0 && h->w_elem == 1) {
+    e4m3_rows_to_f32<<<eval_grid(h), kEvalThreads, 0, st>>>(static_cast<const uint8_t*>(src),
+                                                           h->Wscale, rows, h->k, h->pitch,
+                                                           d_dense);
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? NOMAD_OK : NOMAD_ERR_CUDA;
+  }
   if (h->elem == 2) {
     bf16_rows_to_f32<<<eval_grid(h), kEvalThreads, 0, st>>>(static_cast<const uint16_t*>(src),
                                                            rows, h->k, h->pitch, d_dense);
@@ -292,6 +408,13 @@ int factors_to_f32(nomad_handle* h, int which, float* d_dense, cudaStream_t st) 
 int factors_from_f32(nomad_handle* h, int which, const float* d_dense, cudaStream_t st) {
   const int64_t rows = which == 0 ? h->m : h->n;
   void* dst = which == 0 ? h->W : h->H;
+  if (which == 0 && h->w_elem == 1) {
+    f32_rows_to_e4m3<<<eval_grid(h), kEvalThreads, 0, st>>>(d_dense, rows, h->k, h->k4,
+                                                           h->pitch / 4, static_cast<uint32_t*>(dst),
+                                                           h->Wscale);
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? NOMAD_OK : NOMAD_ERR_CUDA;
+  }
   if (h->elem == 2) {
     f32_rows_to_bf16<<<eval_grid(h), kEvalThreads, 0, st>>>(d_dense, rows, h->k, h->pitch,
                                                            static_cast<uint16_t*>(dst));

@@ -33,6 +33,7 @@ static __device__ __align__(256) int g_range_flag[4];
 struct SymbolAddresses {
   double* partials = nullptr;
   int* flag = nullptr;
+  void* context = nullptr;  // the context the addresses belong to
   bool ready = false;
 };
 
@@ -40,18 +41,43 @@ constexpr int kMaxDevices = 64;
 SymbolAddresses g_addr[kMaxDevices];
 std::mutex g_addr_mutex;
 
+// The current driver context (cuCtxGetCurrent, reached through the runtime so
+// that the library does not link the driver library); null if unavailable.
+void* current_context() {
+  using GetCurrent = int (*)(void**);
+  static GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<GetCurrent>(f);
+  }();
+  void* ctx = nullptr;
+  if (fn == nullptr || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
+
 // Device addresses of the two arrays on the current device.  In host code
 // the symbol names only stand in for the device objects, so the kernels get
-// the addresses returned by cudaGetSymbolAddress, looked up once per device
-// with that device current.
+// the addresses returned by cudaGetSymbolAddress, looked up with the device
+// current: once per device, and again when the device's context is no longer
+// the one the addresses were taken in (after cudaDeviceReset the module is
+// loaded anew and the arrays can move).
 cudaError_t symbol_addresses(int device, SymbolAddresses* out) {
   std::lock_guard<std::mutex> lock(g_addr_mutex);
   SymbolAddresses& a = g_addr[device];
-  if (!a.ready) {
+  // null before the runtime has made the device's context current: then the
+  // lookup below runs and makes it current
+  void* ctx = current_context();
+  if (!a.ready || ctx != a.context) {
+    a.ready = false;
     cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&a.partials), g_partials);
     if (e != cudaSuccess) return e;
     e = cudaGetSymbolAddress(reinterpret_cast<void**>(&a.flag), g_range_flag);
     if (e != cudaSuccess) return e;
+    a.context = current_context();
     a.ready = true;
   }
   *out = a;
@@ -128,9 +154,12 @@ extern "C" int nomad_rmse_noalloc(const float* W, const float* H, int64_t m, int
     return NOMAD_ERR_INVALID_ARG;
   const int64_t tiles = (nnz + kTileRatings - 1) / kTileRatings;
   if (tiles > NOMAD_NOALLOC_MAX_TILES) return NOMAD_ERR_INVALID_ARG;  // over the fixed scratch
+  // An error left pending by the caller's earlier work is reported as
+  // NOMAD_ERR_CUDA and left in place (not consumed) for the caller to read.
+  if (cudaPeekAtLastError() != cudaSuccess) return NOMAD_ERR_CUDA;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) {
-    cudaGetLastError();
+    cudaGetLastError();  // this call's own failure
     return NOMAD_ERR_CUDA;
   }
   SymbolAddresses a;
@@ -149,6 +178,7 @@ extern "C" int nomad_rmse_noalloc(const float* W, const float* H, int64_t m, int
     tile_sq_error<<<unsigned(tiles), kThreads, 0, st>>>(W, H, pitch, k, G, rows, cols, vals, nnz,
                                                        m, n, a.partials, a.flag);
   finish_rmse<<<1, kThreads, 0, st>>>(a.partials, int(tiles), nnz, a.flag, out);
+  // nothing was pending before the launches, so this is their own result
   if (cudaGetLastError() != cudaSuccess) return NOMAD_ERR_CUDA;
   return NOMAD_OK;
 }

@@ -188,10 +188,12 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
       (sched.variant != NOMAD_VARIANT_BATCHED && sched.variant != NOMAD_VARIANT_SIMPLE) ||
       (sched.routing != NOMAD_ROUTING_UNIFORM && sched.routing != NOMAD_ROUTING_SHORTER))
     return NOMAD_ERR_INVALID_ARG;
-  if (sched.precision != NOMAD_FP32 && sched.precision != NOMAD_BF16) return NOMAD_ERR_INVALID_ARG;
-  if (sched.precision == NOMAD_BF16 &&
+  if (sched.precision != NOMAD_FP32 && sched.precision != NOMAD_BF16 &&
+      sched.precision != NOMAD_FP8)
+    return NOMAD_ERR_INVALID_ARG;
+  if (sched.precision != NOMAD_FP32 &&
       (sched.mode != NOMAD_MODE_EPOCH || sched.variant != NOMAD_VARIANT_BATCHED))
-    return NOMAD_ERR_UNSUPPORTED;  // bfloat16 storage: batched epoch-mode kernel only
+    return NOMAD_ERR_UNSUPPORTED;  // narrow storage: batched epoch-mode kernel only
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || sched.device < 0 || sched.device >= ndev) {
     cudaGetLastError();
@@ -206,6 +208,7 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
   h->pitch = h->k4 * 4;
   h->lambda = lambda;
   h->elem = sched.precision == NOMAD_BF16 ? 2 : 4;
+  h->w_elem = sched.precision == NOMAD_BF16 ? 2 : sched.precision == NOMAD_FP8 ? 1 : 4;
   h->sched = sched;
   h->device = sched.device;
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
@@ -226,11 +229,16 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
   h->blocks = (h->p + h->warps_per_block - 1) / h->warps_per_block;
 
   const size_t esz = size_t(h->elem);
+  const size_t wsz = size_t(h->w_elem);
   void* vp = nullptr;
-  if (dev_alloc(h, &vp, esz * size_t(m) * h->pitch) != cudaSuccess) goto oom;
+  if (dev_alloc(h, &vp, wsz * size_t(m) * h->pitch) != cudaSuccess) goto oom;
   h->W = vp;
   if (dev_alloc(h, &vp, esz * size_t(n) * h->pitch) != cudaSuccess) goto oom;
   h->H = vp;
+  if (sched.precision == NOMAD_FP8) {
+    if (dev_alloc(h, &vp, sizeof(float) * size_t(m)) != cudaSuccess) goto oom;
+    h->Wscale = static_cast<float*>(vp);
+  }
   if (dev_alloc(h, &vp, sizeof(int32_t) * kStatusWords) != cudaSuccess) goto oom;
   h->status = static_cast<int32_t*>(vp);
   if (dev_alloc(h, &vp, sizeof(int32_t) * size_t(m)) != cudaSuccess) goto oom;
@@ -247,7 +255,7 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
   if (dev_alloc(h, &vp, sizeof(uint32_t) * 2) != cudaSuccess) goto oom;
   h->log_ticket = static_cast<uint32_t*>(vp);
   if (cudaMemset(h->status, 0, sizeof(int32_t) * kStatusWords) != cudaSuccess) goto cuda_err;
-  if (cudaMemset(h->W, 0, esz * size_t(m) * h->pitch) != cudaSuccess) goto cuda_err;
+  if (cudaMemset(h->W, 0, wsz * size_t(m) * h->pitch) != cudaSuccess) goto cuda_err;
   if (cudaMemset(h->H, 0, esz * size_t(n) * h->pitch) != cudaSuccess) goto cuda_err;
   if (init_factors(h, nullptr) != NOMAD_OK) goto cuda_err;
   if (cudaDeviceSynchronize() != cudaSuccess) goto cuda_err;
@@ -663,7 +671,7 @@ void nomad_destroy(nomad_t* h) {
   DeviceGuard guard(h->device);
   cudaDeviceSynchronize();
   free_layout(h);
-  void** ptrs[] = {&h->W, &h->H, (void**)&h->status, (void**)&h->row_worker,
+  void** ptrs[] = {&h->W, &h->H, (void**)&h->Wscale, (void**)&h->status, (void**)&h->row_worker,
                    (void**)&h->result, (void**)&h->upd_done, (void**)&h->stop,
                    (void**)&h->log_ticket, (void**)&h->step, (void**)&h->partials};
   for (void** p : ptrs) dev_free(h, p);

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 #include <string>
@@ -28,14 +29,10 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
       k.x += 0x9E3779B9u;
       k.y += 0xBB67AE85u;
     }
-#if defined(__CUDA_ARCH__)
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-#else
+    // one widening 32x32->64 multiply gives both halves of each product
     const uint64_t p0 = 0xD2511F53ull * c.x, p1 = 0xCD9E8D57ull * c.z;
     const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
     const uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
-#endif
     c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
   }
   return c;
@@ -95,14 +92,102 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+// ---------------------------------------------------------------- E4M3
+// FP8-E4M3 storage of W (sign, 4 exponent bits with bias 7, 3 mantissa
+// bits; exponent field 0 holds the subnormals m 2^-9; 448 is the largest
+// finite value; 0x7f / 0xff is NaN; no infinity), one binary32 scale per row:
+// the stored value of entry l of row i is scale_i * decode(code_il).
+
+// Exact value of a code.
+__device__ __forceinline__ float e4m3_value(uint32_t c) {
+  const uint32_t e = (c >> 3) & 15u, m = c & 7u;
+  float v = e == 0u ? float(m) * 0x1p-9f : __uint_as_float(((e + 120u) << 23) | (m << 20));
+  if (e == 15u && m == 7u) v = __uint_as_float(0x7fc00000u);
+  return (c & 0x80u) ? -v : v;
+}
+
+// Rounding of a binary32 x to E4M3.  Stochastic (r16 = 16 random bits) or
+// to nearest with ties to even (stochastic = false):
+//  - |x| >= 2^-6: on the bits of |x|, keeping 3 mantissa bits; stochastic
+//    adds r16 << 4 to the 20 dropped bits, nearest adds 0x7ffff plus the
+//    lowest kept bit; magnitudes above 448 saturate to 448;
+//  - |x| < 2^-6: on the grid m 2^-9 (t = |x| 2^9 and its fraction f are
+//    exact in binary32); stochastic rounds up when r16 < f 2^16, nearest when
+//    f > 1/2 or f = 1/2 with floor(t) odd;
+//  - infinities saturate, NaN gives the NaN code.
+// The grid m 2^-9 below 2^-6 (rare after scaling by the row's inverse scale:
+// kept out of line).
+static __device__ __noinline__ uint32_t e4m3_round_small(uint32_t u, bool stochastic, uint32_t r16) {
+  const float t = __fmul_rn(__uint_as_float(u), 512.0f);
+  const float lo = floorf(t);
+  const float f = __fsub_rn(t, lo);
+  const uint32_t m = uint32_t(lo);
+  const bool up = stochastic ? float(r16 & 0xffffu) < __fmul_rn(f, 65536.0f)
+                             : (f > 0.5f || (f == 0.5f && (m & 1u)));
+  return m + (up ? 1u : 0u);
+}
+__device__ __forceinline__ uint32_t e4m3_round(float x, bool stochastic, uint32_t r16) {
+  const uint32_t bits = __float_as_uint(x);
+  const uint32_t sign = (bits >> 24) & 0x80u;
+  uint32_t u = bits & 0x7fffffffu;
+  if (u < 0x3c800000u) return sign | e4m3_round_small(u, stochastic, r16);
+  if (u > 0x7f800000u) return sign | 0x7fu;
+  // |x| >= 2^-6 (infinity included): an integer add and truncation; the
+  // exponent field of the result is at least 121 (2^-6)
+  u += stochastic ? (r16 & 0xffffu) << 4 : 0x7ffffu + ((u >> 20) & 1u);
+  const uint32_t q = (u >> 20) - (120u << 3);  // (E4M3 exponent << 3) | mantissa
+  return sign | (q > 0x7eu ? 0x7eu : q);
+}
+
+// Scale and inverse scale of a row whose largest magnitude is a:
+// s = a / 448, g = 448 / a (binary32 divisions), or 1, 1 for a < 2^-100.
+__device__ __forceinline__ void e4m3_row_scale(float a, float* s, float* g) {
+  if (a >= 0x1p-100f) {
+    *s = __fdiv_rn(a, 448.0f);
+    *g = __fdiv_rn(448.0f, a);
+  } else {
+    *s = 1.0f;
+    *g = 1.0f;
+  }
+}
+
+// Four codes (entry 4c+i in byte i) of the chunk v of a row with inverse
+// scale g; stochastic with ra (entries 0, 1: low and high half) and rb
+// (entries 2, 3), or to nearest.
+__device__ __forceinline__ uint32_t e4m3_pack(float4 v, float g, bool stochastic, uint32_t ra,
+                                              uint32_t rb) {
+  return e4m3_round(__fmul_rn(v.x, g), stochastic, ra) |
+         (e4m3_round(__fmul_rn(v.y, g), stochastic, ra >> 16) << 8) |
+         (e4m3_round(__fmul_rn(v.z, g), stochastic, rb) << 16) |
+         (e4m3_round(__fmul_rn(v.w, g), stochastic, rb >> 16) << 24);
+}
+
+// The chunk's four stored values: s * decode(code), binary32 products.  The
+// codes are decoded by the hardware conversion to half precision, which
+// holds every E4M3 value exactly.
+__device__ __forceinline__ float4 e4m3_unpack(uint32_t c, float s) {
+  uint32_t lo, hi;
+  asm("{\n\t.reg .b16 a, b;\n\tmov.b32 {a, b}, %2;\n\t"
+      "cvt.rn.f16x2.e4m3x2 %0, a;\n\tcvt.rn.f16x2.e4m3x2 %1, b;\n\t}"
+      : "=r"(lo), "=r"(hi) : "r"(c));
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  return make_float4(__fmul_rn(s, a.x), __fmul_rn(s, a.y), __fmul_rn(s, b.x), __fmul_rn(s, b.y));
+}
+
+__device__ __forceinline__ float abs_max4(float4 v, float a) {
+  return fmaxf(a, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+}
+
 // ---------------------------------------------------------------- kernels
 // Status words written by device code: [0] error code (0 = ok), [1] worker,
 // [2] detail, [3] count of ownership violations (debug).
 constexpr int kStatusWords = 4;
 
 struct SgdParams {
-  void* W;                  // m x pitch (fp32 or bf16)
-  void* H;                  // n x pitch
+  void* W;                  // m x pitch (fp32, bf16 or E4M3 codes)
+  void* H;                  // n x pitch (fp32 or bf16)
+  float* Wscale;            // m: the scale of each row of W (E4M3 storage only)
   int32_t pitch;            // elements per row
   int32_t k4;               // 4-element chunks holding the k entries
   const int2* rec;          // {row, value bits} in segment order
@@ -153,12 +238,6 @@ struct SgdParams {
   int32_t drop_item;
 };
 
-struct EvalParams {
-  const void* W;
-  const void* H;
-  int32_t pitch;
-  int32_t k4;
-};
 
 // ---------------------------------------------------------------- handle
 struct DeviceBuf {
@@ -171,7 +250,8 @@ struct DeviceBuf {
 struct nomad_handle {
   int64_t m = 0, n = 0;
   int32_t k = 0, k4 = 0, pitch = 0;
-  int32_t elem = 4;                // bytes per stored entry of W, H
+  int32_t elem = 4;                // bytes per stored entry of H
+  int32_t w_elem = 4;              // bytes per stored entry of W (1: E4M3 codes)
   float lambda = 0.f;
   nomad_schedule sched{};
   int device = 0;
@@ -188,6 +268,7 @@ struct nomad_handle {
   // factors
   void* W = nullptr;
   void* H = nullptr;
+  float* Wscale = nullptr;         // m: row scales of W (E4M3 storage only)
   // layout
   int32_t* row_worker = nullptr;   // m
   int2* rec = nullptr;             // nnz
@@ -254,7 +335,7 @@ int max_resident_workers(int device, int warps_per_block, int k4, int precision,
 int default_warps_per_block();
 // Batched epoch-mode worker kernel (epoch_batched.cu): pointer and dynamic
 // shared memory per warp in bytes; nullptr for an unsupported k4.
-const void* batched_kernel(int k4, bool debug, bool bf16, bool many, size_t* smem_per_warp);
+const void* batched_kernel(int k4, bool debug, int precision, bool many, size_t* smem_per_warp);
 
 // Initialisation, evaluation and factor copies (eval.cu).
 int init_factors(nomad_handle* h, cudaStream_t stream);

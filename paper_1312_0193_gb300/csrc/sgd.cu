@@ -370,8 +370,8 @@ const void* worker_kernel(int k4, bool debug, int mode, int variant, int precisi
                           size_t* smem_per_warp) {
   *smem_per_warp = 0;
   if (mode == NOMAD_MODE_EPOCH && variant == NOMAD_VARIANT_BATCHED)
-    return batched_kernel(k4, debug, precision == NOMAD_BF16, false, smem_per_warp);
-  if (precision != NOMAD_FP32) return nullptr;  // bfloat16 storage: batched kernel only
+    return batched_kernel(k4, debug, precision, false, smem_per_warp);
+  if (precision != NOMAD_FP32) return nullptr;  // narrow storage: batched kernel only
   if (k4 <= 32) return epoch_kernel_ptr<1>(debug, mode);
   if (k4 <= 64) return epoch_kernel_ptr<2>(debug, mode);
   if (k4 <= 128) return epoch_kernel_ptr<4>(debug, mode);
@@ -419,6 +419,7 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
   P = SgdParams{};
   P.W = h->W;
   P.H = h->H;
+  P.Wscale = h->Wscale;
   P.pitch = h->pitch;
   P.k4 = h->k4;
   P.rec = h->rec;
@@ -541,7 +542,7 @@ int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cud
   const bool debug = h0->sched.debug != 0;
   const int wpb = h0->warps_per_block;
   size_t spw = 0;
-  const void* fn = batched_kernel(h0->k4, debug, h0->sched.precision == NOMAD_BF16, true, &spw);
+  const void* fn = batched_kernel(h0->k4, debug, h0->sched.precision, true, &spw);
   if (!fn) return NOMAD_ERR_UNSUPPORTED;
   const size_t smem = spw * size_t(wpb) + ((sizeof(SgdParams) + 15) & ~size_t(15));
   if (smem > 48 * 1024 &&

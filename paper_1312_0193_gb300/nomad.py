@@ -31,6 +31,7 @@ NOMAD_MODE_EPOCH = 0
 NOMAD_MODE_UNIFORM = 1
 NOMAD_FP32 = 0
 NOMAD_BF16 = 1
+NOMAD_FP8 = 2
 NOMAD_PARTITION_RATINGS = 0
 NOMAD_PARTITION_USERS = 1
 NOMAD_VARIANT_BATCHED = 0
@@ -232,7 +233,7 @@ class Nomad:
         s = nomad_schedule_default()
         s.alpha, s.beta = alpha, beta
         s.mode = {"epoch": NOMAD_MODE_EPOCH, "uniform": NOMAD_MODE_UNIFORM}[mode]
-        s.precision = {"fp32": NOMAD_FP32, "bf16": NOMAD_BF16}[precision]
+        s.precision = {"fp32": NOMAD_FP32, "bf16": NOMAD_BF16, "fp8": NOMAD_FP8}[precision]
         s.partition = {"ratings": NOMAD_PARTITION_RATINGS,
                        "users": NOMAD_PARTITION_USERS}[partition]
         s.n_workers = n_workers

@@ -69,6 +69,17 @@ class Ratings:
                        t(self.train_vals), t(self.test_rows), t(self.test_cols),
                        t(self.test_vals), self.name)
 
+    def fingerprint(self) -> list:
+        """Sums of the index and value arrays (train and test): two runs of a
+        generator gave the same data when these agree."""
+        f = lambda t: t.detach().cpu().numpy()
+        return [int(f(self.train_rows).astype(np.int64).sum()),
+                int(f(self.train_cols).astype(np.int64).sum()),
+                float(f(self.train_vals).astype(np.float64).sum()),
+                int(f(self.test_rows).astype(np.int64).sum()),
+                int(f(self.test_cols).astype(np.int64).sum()),
+                float(f(self.test_vals).astype(np.float64).sum())]
+
     def stats(self) -> dict:
         r = self.train_rows.long()
         c = self.train_cols.long()
@@ -391,13 +402,24 @@ def yahoo_shaped(scale: float = 1.0, seed: int = 3, device="cpu") -> Ratings:
                   "yahoo-shaped-x%g" % scale)
 
 
-def hugewiki_shaped(scale: float = 1.0, seed: int = 4, device="cpu") -> Ratings:
+def hugewiki_shaped(scale: float = 1.0, seed: int = 4, device="cpu",
+                    item_s: float = 0.8, name: str = "hugewiki-shaped") -> Ratings:
     """Hugewiki-shaped: m=50,082,603, n=39,780, ~2.74B train ratings (mean
-    54.6 per row; mild Zipf(0.5) over rows and Zipf(0.8) over columns) + 1%
-    test; real values <u,v> + N(0, 0.1^2) from a planted rank-100 model."""
+    54.6 per row; mild Zipf(0.5) over rows and Zipf(item_s) over columns) +
+    1% test; real values <u,v> + N(0, 0.1^2) from a planted rank-100 model.
+    With the default Zipf(0.8) over columns the weights of the top items
+    exceed m and are capped: the most-rated item is rated by every user
+    (50.1M ratings at full size), a property of this generator, not of the
+    paper's data (whose mean is 68,635 ratings per item)."""
     m = max(64, int(round(50_082_603 * scale)))
     n = max(32, int(round(39_780 * math.sqrt(scale))))
     nnz = int(round(2_736_496_604 * scale))
-    return skewed(m, n, nnz, nnz // 100, 0.5, 0.8, 100, hugewiki_value, seed,
-                  device, name="hugewiki-shaped" if scale == 1.0 else
-                  "hugewiki-shaped-x%g" % scale)
+    return skewed(m, n, nnz, nnz // 100, 0.5, item_s, 100, hugewiki_value, seed,
+                  device, name=name if scale == 1.0 else "%s-x%g" % (name, scale))
+
+
+def hugewiki_flat(scale: float = 1.0, seed: int = 4, device="cpu") -> Ratings:
+    """Hugewiki-shaped with flatter column degrees, Zipf(0.5): no column
+    reaches the cap m, and the most-rated item holds about 0.25% of the
+    ratings (about 6.9M of 2.74B at full size, 14% of the users)."""
+    return hugewiki_shaped(scale, seed, device, item_s=0.5, name="hugewiki-flat")

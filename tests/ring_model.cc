@@ -15,10 +15,15 @@
 //  fifo    one token at a time at the ring's head; capacity >= the worker's
 //          segments;
 //  window  the batched kernel's: the first kWindow positions are read, up
-//          to kBatch ready ones are taken (a position reserved but not yet
-//          written does not hold back the ones behind it), the head moves
-//          past the taken prefix, and the batch's tokens are handed on
-//          together at its end; capacity >= segments + kWindow + 1.  The
+//          to B ready ones are taken (B = 16, the kernel's batch when a row
+//          is one 16-byte chunk per lane; mode window8: B = 8, its batch for
+//          wider rows; a position reserved but not yet written does not hold
+//          back the ones behind it), the head moves past the taken prefix,
+//          the batch's long visits (a fixed quarter of the segments, as the
+//          kernel's visits of >= 32 ratings) run first and each is handed on
+//          right after its visit, and the other tokens are handed on
+//          together at the end of the batch; capacity >= segments +
+//          kWindow + 1.  The
 //          tokens of urgent items (at least half the segments of the
 //          item with most) travel through a second ring per worker
 //          (capacity >= urgent items + 1), taken one at a time before each
@@ -31,7 +36,7 @@
 //          | stall (one worker sleeps between visits)
 //          | slowpub (some producers pause between reserving and writing)
 //          | smallring (rings of a quarter of the segments: a planted mistake)
-//   mode:  fifo (default) | window
+//   mode:  fifo (default) | window | window8
 // prints: status=<ok|timeout|ownership|overwrite> visits=<v> expected=<S*E>
 //         exact_once=<0|1> per_item_epochs_ok=<0|1> urgent_items=<u>
 #include <algorithm>
@@ -49,13 +54,13 @@
 namespace {
 
 constexpr int kWindow = 16;
-constexpr int kBatch = 8;
 
 struct Model {
   int p = 0, n = 0, epochs = 0;
   uint64_t seed = 0;
   std::string fault;
   bool window = false;
+  int batch = 16;  // tokens taken at once (window disciplines)
   // layout: segments per item, each with a worker
   std::vector<int> seg_worker, seg_item;
   std::vector<std::vector<int>> item_segs;    // segments of item j
@@ -81,8 +86,8 @@ struct Model {
   std::atomic<uint32_t> pushes{0};
   std::atomic<int64_t> total{0};
 
-  Model(int p_, int n_, int maxdeg, int e_, uint64_t s_, std::string f, bool win)
-      : p(p_), n(n_), epochs(e_), seed(s_), fault(std::move(f)), window(win),
+  Model(int p_, int n_, int maxdeg, int e_, uint64_t s_, std::string f, bool win, int b_)
+      : p(p_), n(n_), epochs(e_), seed(s_), fault(std::move(f)), window(win), batch(b_),
         slots(0), taken_lap(0), uslots(0), utail(p_), utaken_lap(0), tail(p_), owner(n_),
         visits(0) {
     std::mt19937_64 rng(seed);
@@ -270,21 +275,29 @@ struct Model {
         continue;
       }
       t_last = std::chrono::steady_clock::now();
-      std::vector<int> batch;
-      for (int i = 0; i < kWindow && int(batch.size()) < kBatch; ++i) {
+      std::vector<int> longv, shortv;
+      int taken_now = 0;
+      for (int i = 0; i < kWindow && taken_now < batch; ++i) {
         if (!((ready >> i) & 1u)) continue;
         const uint32_t pos = head + uint32_t(i);
         taken_lap[base[q] + (pos & mask)].store(pos >> lg, std::memory_order_release);
         taken |= 1u << i;
-        batch.push_back(got[i]);
+        (is_long(got[i]) ? longv : shortv).push_back(got[i]);
+        ++taken_now;
       }
       while (taken & 1u) {  // the head moves past the taken prefix
         taken >>= 1;
         ++head;
       }
-      done += int64_t(batch.size());
+      done += int64_t(taken_now);
+      for (int seg : longv) {  // long visits first, each handed on at once
+        while (try_urgent()) {
+        }
+        const int nx = visit(q, seg);
+        if (nx >= 0) push(seg_worker[nx], nx);
+      }
       std::vector<int> next;
-      for (int seg : batch) {
+      for (int seg : shortv) {
         while (try_urgent()) {
         }
         next.push_back(visit(q, seg));
@@ -293,6 +306,9 @@ struct Model {
         if (nseg_id >= 0) push(seg_worker[nseg_id], nseg_id);
     }
   }
+
+  // a fixed quarter of the segments stand for the kernel's long visits
+  static bool is_long(int seg) { return ((uint32_t(seg) * 2654435761u) >> 30) == 0; }
 
   void worker(int q) {
     if (window) {
@@ -350,12 +366,13 @@ struct Model {
 
 int main(int argc, char** argv) {
   if (argc != 7 && argc != 8) {
-    std::fprintf(stderr, "usage: ring_model p n maxdeg epochs seed fault [fifo|window]\n");
+    std::fprintf(stderr, "usage: ring_model p n maxdeg epochs seed fault [fifo|window|window8]\n");
     return 2;
   }
-  const bool window = argc == 8 && std::string(argv[7]) == "window";
+  const std::string mode = argc == 8 ? argv[7] : "fifo";
+  const bool window = mode == "window" || mode == "window8";
   Model M(std::atoi(argv[1]), std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]),
-          std::strtoull(argv[5], nullptr, 10), argv[6], window);
+          std::strtoull(argv[5], nullptr, 10), argv[6], window, mode == "window8" ? 8 : 16);
   M.run();
   const int64_t S = int64_t(M.seg_worker.size());
   bool exact = true;

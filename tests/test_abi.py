@@ -111,3 +111,17 @@ def test_no_gpu_fails_loudly(lib):
     with pytest.raises(nb.NomadError) as e:
         nb.Nomad(10, 10, 4, 0.1)
     assert e.value.code == nb.NOMAD_ERR_CUDA
+
+
+def test_binding_constants_match_header():
+    """Every NOMAD_* integer constant of the header has the same value in
+    the binding (precision, modes, error codes, ...)."""
+    from paper_1312_0193_gb300 import nomad as nb
+    with open(HEADER) as f:
+        src = f.read()
+    defs = dict(re.findall(r"#define\s+(NOMAD_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src))
+    assert "NOMAD_FP8" in defs
+    for name, val in defs.items():
+        if name in ("NOMAD_H_", "NOMAD_NOALLOC_MAX_TILES"):
+            continue
+        assert getattr(nb, name) == int(val), name

@@ -1,0 +1,173 @@
+"""FP8-E4M3 storage of W on the GPU (one binary32 scale per row, H in
+binary32, binary32 arithmetic, stochastic rounding of W at every update)
+against the oracle's E4M3 replay (reading R15).
+
+Tolerance of the replay comparison.  Both sides take the same stochastic
+rounding draws (the bfloat16 rule's Philox counters), decode with the same
+binary32 product scale * value and round w * g with g = 448 / max|w| in
+binary32.  The binary32 values they round differ by a few units in the last
+place (the GPU sums the dot product as a lane tree and fuses multiply-adds;
+the oracle sums left to right).  Such a difference changes a stored value in
+one of two ways:
+ - through the row's largest magnitude, the scale moves by an ulp: every
+   stored value of the row moves by about 2^-23 relative;
+ - a code flips when the value sits within the difference of a rounding
+   threshold: the 20 dropped bits take 16 random bits at their top, so the
+   chance is about 2^-20 per written entry; the entry then moves by one E4M3
+   step, up to 1/8 of its value, and later updates carry the change.
+A flip moves h_j of the visit by a noticeable amount, which shifts every
+later binary32 value computed from it by much more than an ulp, so later
+rounding decisions then differ with a probability of order (shift / step):
+the two runs drift apart over epochs (15% of W's entries differ after 10
+epochs of the tiny problem at alpha 0.05).  Parity is therefore tested where
+it is exact and where the drift has not begun:
+ - with a zero step both sides round bit-identical values: W and H must be
+   equal bit for bit (this checks decoding, scales, the draws, the rounding
+   and the forwarding of rows between positions in flight);
+ - one epoch at a small step: an entry counts as flipped when it differs by
+   more than 1e-3 relative (one E4M3 step is at least 1/16 of the value; a
+   scale that moved by an ulp moves the value by 1.2e-7).  The relative L2
+   distance must stay below 5e-2.  In the stream of short visits at most 2%
+   of W's entries may be flipped.  With 4 workers the visits are long and
+   run in block form, whose e_u (the algebraically equal block recurrence)
+   rounds differently from the sequential update by a few ulps per rating;
+   along a chain of hundreds of ratings h then drifts by about 1e-3 relative
+   (measured 1.8e-3), so a later rounding differs with probability about
+   8 x 1e-3 per entry write and its flips cascade: up to 25% of the entries
+   may be flipped there (measured 15%).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1312_0193_gb300 import Nomad, NomadError  # noqa: E402
+from paper_1312_0193_gb300 import nomad as nb  # noqa: E402
+
+FP8_REPLAY_TOL = 5e-2
+FP8_DIFF_FRAC = 0.02
+REDUCE_TOL = 1e-6
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oracle_init_w(rows, k, seed):
+    """The oracle's initial W (Sec. 5.1 values) stored as E4M3 rounded to
+    nearest: (codes, scales)."""
+    return oracle.e4m3_rows(oracle.init_factor(rows, k, seed, 0).astype(np.float32))
+
+
+@pytest.mark.parametrize("k,seed", [(10, 2), (100, 7), (130, 5)])
+def test_fp8_init_bit_exact(k, seed):
+    with Nomad(300, 170, k, 0.05, seed=seed, precision="fp8") as nm:
+        W, H = nm.factors()
+    codes, scales = oracle_init_w(300, k, seed)
+    assert np.array_equal(W, oracle.e4m3_decode_rows(codes, scales))
+    assert np.array_equal(H.astype(np.float64), oracle.init_factor(170, k, seed, 1))
+
+
+def test_fp8_only_with_batched_epoch_kernel():
+    with pytest.raises(NomadError) as e:
+        Nomad(10, 10, 4, 0.1, precision="fp8", variant="simple")
+    assert e.value.code == nb.NOMAD_ERR_UNSUPPORTED
+    with pytest.raises(NomadError):
+        Nomad(10, 10, 4, 0.1, precision="fp8", mode="uniform")
+
+
+def fp8_replay(r, k, p, epochs, alpha, lam=0.05, beta=0.05, seed=11):
+    """A debug run on the GPU and the oracle's E4M3 replay of its logged
+    order from the oracle's own initial factors: (GPU W, H, oracle W, H)."""
+    tr, tc, tv, *_ = r.numpy()
+    with Nomad(r.m, r.n, k, lam, alpha=alpha, beta=beta, debug=True, n_workers=p, seed=seed,
+               precision="fp8") as nm:
+        nm.load_coo(r.train_rows.cuda(), r.train_cols.cuda(), r.train_vals.cuda())
+        rw = oracle.partition_rows(r.m, tr, p)
+        L = oracle.build_layout(r.m, r.n, tr, tc, tv, rw, p)
+        W0, H0 = nm.factors()
+        nm.epoch(epochs)
+        nm.check()
+        seg, ep = nm.replay_log()
+        Wg, Hg = nm.factors()
+        counts, viol = nm.debug_counts()
+    assert viol == 0 and np.all(counts == epochs)
+    c0, s0 = oracle_init_w(r.m, k, seed)
+    assert np.array_equal(W0, oracle.e4m3_decode_rows(c0, s0))
+    assert np.array_equal(H0.astype(np.float64), oracle.init_factor(r.n, k, seed, 1))
+    Wc, Ws, Ho, cnt = oracle.replay_e4m3(L, seg, ep, c0, s0, H0, float(np.float32(lam)),
+                                         float(np.float32(alpha)), float(np.float32(beta)),
+                                         seed)
+    assert np.array_equal(cnt, counts)
+    return Wg, Hg, oracle.e4m3_decode_rows(Wc, Ws), Ho
+
+
+@pytest.mark.parametrize("k,p", [(10, 64), (100, 40), (100, 4)])
+def test_fp8_replay_zero_step_bit_exact(k, p):
+    """With a zero step both sides hold bit-identical binary32 values at
+    every write (w' = w, h' = h), so every stochastic rounding decision,
+    every re-derived scale and every forwarded row must agree exactly: the
+    GPU's stored W equals the oracle's replay bit for bit.  p = 4 gives long
+    visits (the block form) and rows forwarded between positions in flight."""
+    r = synth.tiny_planted(1) if k == 10 else synth.netflix_shaped(0.0005, seed=3)
+    Wg, Hg, Wo, Ho = fp8_replay(r, k, p, 2, 0.0)
+    assert np.array_equal(Wg, Wo)
+    assert np.array_equal(Hg, Ho)
+
+
+@pytest.mark.parametrize("k,p,flip_frac", [(10, 64, FP8_DIFF_FRAC), (100, 40, FP8_DIFF_FRAC),
+                                           (100, 4, 0.25)])
+def test_fp8_replay_one_epoch(k, p, flip_frac):
+    """One epoch at a small step (alpha 0.01): integer accounting bit-exact,
+    factors within the derived bound."""
+    r = synth.tiny_planted(1) if k == 10 else synth.netflix_shaped(0.0005, seed=3)
+    Wg, Hg, Wo, Ho = fp8_replay(r, k, p, 1, 0.01)
+    d = np.abs(Wg.astype(np.float64) - Wo) > 1e-3 * np.abs(Wo.astype(np.float64))
+    frac = float(np.mean(d))
+    print("fp8 replay k=%d p=%d: flipped %.4f, rel W %.3e, rel H %.3e" % (
+        k, p, frac, rel(Wg, Wo), rel(Hg, Ho)))
+    assert frac <= flip_frac, frac
+    assert rel(Wg, Wo) < FP8_REPLAY_TOL and rel(Hg, Ho) < FP8_REPLAY_TOL, (rel(Wg, Wo), rel(Hg, Ho))
+
+
+def test_fp8_factors_roundtrip_and_rmse():
+    r = synth.tiny_planted(1)
+    tr, tc, tv, er, ec, ev = r.numpy()
+    rng = np.random.default_rng(4)
+    W = rng.normal(size=(r.m, 10)).astype(np.float32)
+    W[7] = 0.0  # a zero row keeps scale 1
+    H = rng.normal(size=(r.n, 10)).astype(np.float32)
+    with Nomad(r.m, r.n, 10, 0.05, precision="fp8") as nm:
+        nm.load_coo(r.train_rows.cuda(), r.train_cols.cuda(), r.train_vals.cuda())
+        nm.set_factors(W, H)
+        W2, H2 = nm.factors()
+        got = nm.rmse(er, ec, ev)
+        J = nm.objective()
+    assert np.array_equal(W2, oracle.e4m3_decode_rows(*oracle.e4m3_rows(W)))
+    assert np.array_equal(H2, H)
+    want = oracle.rmse(er, ec, ev, W2.astype(np.float64), H2.astype(np.float64))
+    assert abs(got - want) <= REDUCE_TOL * want
+    Jw = oracle.objective(tr, tc, tv, W2.astype(np.float64), H2.astype(np.float64),
+                          float(np.float32(0.05)))
+    assert abs(J - Jw) <= REDUCE_TOL * Jw
+
+
+def test_fp8_free_run_quality_close_to_fp32():
+    """20 epochs at the paper's schedule: the E4M3 run's test RMSE is within
+    1.5% of the binary32 run's (the oracle's own E4M3 replay stays within 1%
+    of its binary32 replay; the free runs' visit orders add 0.5%)."""
+    r = synth.tiny_planted(1)
+    er, ec, ev = r.numpy()[3:]
+    out = {}
+    for prec in ("fp32", "fp8"):
+        with Nomad(r.m, r.n, 10, 0.05, precision=prec) as nm:
+            nm.load_coo(r.train_rows.cuda(), r.train_cols.cuda(), r.train_vals.cuda())
+            nm.epoch(20)
+            out[prec] = nm.rmse(er, ec, ev)
+    assert abs(out["fp8"] - out["fp32"]) <= 0.015 * out["fp32"], out

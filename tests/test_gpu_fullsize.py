@@ -73,6 +73,11 @@ def test_fullsize_epoch_replay_and_rmse(netflix, oracle_layout_full):
     for g, o in ((Wg, Wo), (Hg, Ho)):
         d = np.linalg.norm(g.astype(np.float64) - o) / np.linalg.norm(o.astype(np.float64))
         assert d < 1e-4, d
+        # every row on its own: one skipped or doubled update moves one row by
+        # a whole step, which the norm over 48M entries could hide
+        g64, o64 = g.astype(np.float64), o.astype(np.float64)
+        rows = np.linalg.norm(g64 - o64, axis=1) / np.maximum(np.linalg.norm(o64, axis=1), 1e-30)
+        assert rows.max() < 1e-3, rows.max()
     want = oracle.rmse(er, ec, ev, Wg.astype(np.float64), Hg.astype(np.float64))
     assert abs(got_rmse - want) <= 1e-6 * want
 
