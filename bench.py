@@ -28,10 +28,11 @@ oracle instead (rank 0 only).
 
 --sweep N: N independent seeded problems of random shape, k and lambda
 (synth.sweep_specs), one epoch each per step, run as one persistent launch
-(nomad_epoch_many; blocks in proportion to each problem's ratings, then
-re-allocated from each problem's measured device time span) and, as
-the baseline, as N launches one after another (each problem alone on every
-resident warp).
+(nomad_epoch_many) with per-problem knobs picked by an autotuner (workers,
+the circulation of the tokens, tokens taken at once; from calibration
+launches and each problem's measured device time span) and, as the
+baseline, as N launches one after another (each problem alone on every
+resident warp); the tuned launch is also timed with bfloat16 storage.
 """
 from __future__ import annotations
 
@@ -414,44 +415,74 @@ def run_sweep(args):
     wpb = 8
     alpha, beta = 0.012, 0.05
 
-    def handles(workers):
+    def handles(knobs, precision="fp32"):
         out = []
-        for sp, r, p in zip(specs, probs, workers):
+        for sp, r, kn in zip(specs, probs, knobs):
             nm = Nomad(r.m, r.n, sp["k"], sp["lam"], alpha=alpha, beta=beta, device=local,
-                       n_workers=p, warps_per_block=wpb)
+                       n_workers=kn["blocks"] * wpb, warps_per_block=wpb, precision=precision,
+                       circulation=kn["circulation"], batch_tokens=kn["batch_tokens"])
             nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
             out.append(nm)
         return out
 
-    # blocks in proportion to the ratings, then --sweep-tune rounds of: one
-    # epoch in one launch, each problem's device time span read back, blocks
-    # in proportion to each problem's block-seconds (span x blocks); the
-    # allocation measured fastest is kept (a problem's span does not fall in
-    # proportion to its blocks: more workers also lengthen each item's chain
-    # of visits)
-    blocks = sweep_blocks(nnz, sms)
-    tuning = []
-    best = None
-    for _ in range(args.sweep_tune):
-        cal = handles([b * wpb for b in blocks])
+    def calibrate(knobs):
+        """One epoch of every problem in one launch: (kernel ms, span ns per
+        problem)."""
+        cal = handles(knobs)
         Nomad.epoch_many(cal, 1)
         ms = cal[0].last_epoch_kernel_ms()
         spans = [nm.last_epoch_span_ns() for nm in cal]
         for nm in cal:
             nm.close()
-        tuning.append({"blocks": blocks, "kernel_ms": round(ms, 2),
+        return ms, spans
+
+    # The autotuner.  Knobs per problem: its blocks (workers = 8 x blocks),
+    # the circulation of its tokens (flat, or the hybrid of Sec. 3.4) and the
+    # tokens a worker takes at once (16 or 8).  Start: blocks in proportion
+    # to the ratings, flat, 16.  Each knob is chosen per problem from
+    # calibration launches (every problem's device time span read back; the
+    # launch waits for its slowest problem), then --sweep-tune rounds
+    # re-allocate the blocks in proportion to each problem's block-seconds
+    # (span x blocks); the allocation measured fastest is kept.  Queue
+    # capacity and the chunks per lane are not knobs: a ring holds every
+    # token a worker can be sent, and a lane holds ceil(k / 128) chunks.
+    knobs = [{"blocks": b, "circulation": "flat", "batch_tokens": 0}
+             for b in sweep_blocks(nnz, sms)]
+    tuning = []
+
+    def trial(kn, what):
+        ms, spans = calibrate(kn)
+        tuning.append({"trial": what, "kernel_ms": round(ms, 2),
                        "slowest_span_ms": round(max(spans) / 1e6, 2),
                        "mean_span_ms": round(statistics.mean(spans) / 1e6, 2)})
-        if best is None or ms < best[0]:
-            best = (ms, blocks)
-        new = sweep_blocks([max(sp, 1) * b for sp, b in zip(spans, blocks)], sms)
-        if new == blocks:
-            break
-        blocks = new
-    if best is not None:
-        blocks = best[1]
-    many = handles([b * wpb for b in blocks])
-    alone = handles([0] * len(specs))
+        return ms, spans
+
+    best = None
+    if args.sweep_tune > 0:
+        ms_flat, sp_flat = trial(knobs, "flat circulation, 16 tokens")
+        alt = [dict(k, circulation="block") for k in knobs]
+        ms_blk, sp_blk = trial(alt, "hybrid circulation, 16 tokens")
+        knobs = [dict(k, circulation="block" if b < f else "flat")
+                 for k, f, b in zip(knobs, sp_flat, sp_blk)]
+        ms16, sp16 = trial(knobs, "per-problem circulation, 16 tokens")
+        alt = [dict(k, batch_tokens=8) for k in knobs]
+        ms8, sp8 = trial(alt, "per-problem circulation, 8 tokens")
+        knobs = [dict(k, batch_tokens=8 if e < s_ else 0)
+                 for k, s_, e in zip(knobs, sp16, sp8)]
+        ms, spans = trial(knobs, "per-problem circulation and tokens")
+        best = (ms, [dict(k) for k in knobs])
+        for _ in range(args.sweep_tune):
+            blocks = sweep_blocks([max(sp, 1) * k["blocks"] for sp, k in zip(spans, knobs)],
+                                  sms)
+            if blocks == [k["blocks"] for k in knobs]:
+                break
+            knobs = [dict(k, blocks=b) for k, b in zip(knobs, blocks)]
+            ms, spans = trial(knobs, "blocks re-allocated")
+            if ms < best[0]:
+                best = (ms, [dict(k) for k in knobs])
+        knobs = best[1]
+    many = handles(knobs)
+    alone = handles([{"blocks": 0, "circulation": "flat", "batch_tokens": 0}] * len(specs))
     stream = torch.cuda.current_stream(dev)
 
     def run_many():
@@ -466,7 +497,7 @@ def run_sweep(args):
         run_alone()
     torch.cuda.synchronize(dev)
     launches0 = sum(nm.info()["kernel_launches"] for nm in many)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     kern_many = []
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -483,17 +514,30 @@ def run_sweep(args):
         run_alone()
     ev[3].record(stream)
     torch.cuda.synchronize(dev)
+    # the same tuned launch with bfloat16 storage
+    many_bf = handles(knobs, precision="bf16")
+    for _ in range(args.warmup):
+        Nomad.epoch_many(many_bf, 1)
+    torch.cuda.synchronize(dev)
+    ev[4].record(stream)
+    for _ in range(args.steps):
+        Nomad.epoch_many(many_bf, 1)
+    ev[5].record(stream)
+    torch.cuda.synchronize(dev)
     barrier(world)
     t_many, units = reduce_max_sum(ev[0].elapsed_time(ev[1]) / 1e3, total * args.steps, world, dev)
     t_seq, _ = reduce_max_sum(ev[2].elapsed_time(ev[3]) / 1e3, total * args.steps, world, dev)
-    # the same problems after the same epochs: test RMSE of both arms (the
+    t_bf, _ = reduce_max_sum(ev[4].elapsed_time(ev[5]) / 1e3, total * args.steps, world, dev)
+    # the same problems after the same epochs: test RMSE of the arms (the
     # worker counts differ, so the visit orders and the iterates do too)
-    rm_many, rm_alone = [], []
-    for a, b, r in zip(many, alone, probs):
+    rm_many, rm_alone, rm_bf = [], [], []
+    for a, b, c, r in zip(many, alone, many_bf, probs):
         a.check()
         b.check()
+        c.check()
         rm_many.append(a.rmse(r.test_rows, r.test_cols, r.test_vals))
         rm_alone.append(b.rmse(r.test_rows, r.test_cols, r.test_vals))
+        rm_bf.append(c.rmse(r.test_rows, r.test_cols, r.test_vals))
     bytes_upd = sum(n * (2 * sp["k"] * 4 + 8) for n, sp in zip(nnz, specs))
     kern_s = statistics.mean(kern_many) / 1e3
     peak, peak_src = load_peaks()
@@ -511,7 +555,9 @@ def run_sweep(args):
                             "density~U[0.1%%,2%%], k in {16,32,64,128}, lambda in "
                             "{0.01,0.05,0.1,0.5}; %.3g train ratings" % (len(specs), total),
                 "alpha": alpha, "beta": beta, "step": "one epoch of every problem",
-                "blocks": blocks, "warps_per_block": wpb, "tuning": tuning,
+                "warps_per_block": wpb, "tuning": tuning,
+                "knobs": [dict(k, problem=i, workers=k["blocks"] * wpb, k=sp["k"], nnz=n)
+                          for i, (k, sp, n) in enumerate(zip(knobs, specs, nnz))],
                 "l2": "inputs larger than L2 (ratings %.1f GB); no flush" % (total * 8 / 1e9),
                 "generate_seconds": round(gen_s, 1),
                 "parallelism": "replicas x%d" % world,
@@ -521,6 +567,9 @@ def run_sweep(args):
                            "step": "%d nomad_epoch calls, each problem on every resident warp"
                                    % len(specs)},
             "speedup_vs_sequential": t_seq / t_many,
+            "bf16": {"value": units / t_bf, "unit": UNIT, "ms_per_step": t_bf * 1e3 / args.steps,
+                     "step": "the tuned one-launch sweep with bfloat16 storage",
+                     "test_rmse_mean": statistics.mean(rm_bf)},
             "test_rmse": {"epochs": args.warmup + args.steps,
                           "one_launch_mean": statistics.mean(rm_many),
                           "sequential_mean": statistics.mean(rm_alone),
@@ -535,7 +584,7 @@ def run_sweep(args):
             "clocks": clocks.summary(),
         }
         print(json.dumps(out), flush=True)
-    for nm in many + alone:
+    for nm in many + alone + many_bf:
         nm.close()
     if world > 1:
         import torch.distributed as dist
@@ -587,8 +636,9 @@ def run_gaps(args):
     """Test-RMSE gap to the binary64 oracle per workload and storage format:
     every workload of tests/golden/rmse_targets.json (data generated on the
     CPU from its seed, as the oracle's target script did), E epochs of the
-    timed kernel from the library's initial factors, against the oracle's
-    test RMSE after the same E epochs.  One JSON line per (workload,
+    timed kernel with p workers from the library's initial factors, against
+    the oracle's serial NOMAD with the same p after the same E epochs (and,
+    for reference, its textbook shuffled SGD).  One JSON line per (workload,
     format), then a summary line."""
     import torch
     import synth
@@ -601,12 +651,13 @@ def run_gaps(args):
     rows = []
     for key in sorted(targets):
         t = targets[key]
-        if t["config"] not in gens:
+        if t.get("config") not in gens or "nomad" not in t:
             continue
         r = getattr(synth, gens[t["config"]])(t["scale"], device="cpu").to(dev)
         for prec in ("fp32", "bf16", "fp8"):
             nm = Nomad(r.m, r.n, t["k"], t["lambda"], alpha=t["alpha"], beta=t["beta"],
-                       seed=int(t["init_seed"]), precision=prec)
+                       seed=int(t["init_seed"]), precision=prec,
+                       n_workers=int(t["nomad"]["p"]))
             nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
             ms = 0.0
             for _ in range(int(t["epochs"])):
@@ -615,10 +666,17 @@ def run_gaps(args):
             nm.check()
             got = nm.rmse(r.test_rows, r.test_cols, r.test_vals)
             nm.close()
-            want = float(t["test_rmse"][-1])
+            want = float(t["nomad"]["test_rmse"])
+            want_sd = float(t["nomad"].get("test_rmse_std", 0.0))
+            shuf = float(t["test_rmse"][-1])
             row = {"workload": t["workload"], "nnz_train": t["nnz_train"], "precision": prec,
-                   "epochs": int(t["epochs"]), "gpu_test_rmse": got, "oracle_test_rmse": want,
-                   "gap_pct": 100.0 * (got / want - 1.0), "gpu_seconds": ms / 1e3}
+                   "epochs": int(t["epochs"]), "workers": int(t["nomad"]["p"]),
+                   "gpu_test_rmse": got, "oracle_nomad_test_rmse": want,
+                   "oracle_nomad_std": want_sd,
+                   "oracle_nomad_draws": len(t["nomad"].get("runs", [1])),
+                   "gap_pct": 100.0 * (got / want - 1.0),
+                   "oracle_shuffled_sgd_test_rmse": shuf,
+                   "gap_to_shuffled_pct": 100.0 * (got / shuf - 1.0), "gpu_seconds": ms / 1e3}
             rows.append(row)
             print(json.dumps(row), flush=True)
         del r
@@ -631,7 +689,9 @@ def kernel_rev():
     to the code they were taken from."""
     import hashlib
     hs = hashlib.sha256()
-    for name in ("epoch_batched.cu", "sgd_common.cuh"):
+    for name in ("epoch_batched.cuh", "epoch_batched.cu", "epoch_batched_f32.cu",
+                 "epoch_batched_bf16.cu", "epoch_batched_fp8.cu", "sgd_common.cuh",
+                 "nomad_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1312_0193_gb300", "csrc", name), "rb") as f:
             hs.update(f.read())
     return hs.hexdigest()[:16]
@@ -702,7 +762,9 @@ def main(argv=None):
     ap.add_argument("--sweep", type=int, default=0,
                     help="time N independent problems in one launch against N launches")
     ap.add_argument("--sweep-tune", type=int, default=2,
-                    help="rounds of block re-allocation from measured per-problem spans")
+                    help="autotuner: 0 = no tuning; else per-problem circulation and batch "
+                         "size from calibration launches, then this many rounds of block "
+                         "re-allocation from measured per-problem spans")
     ap.add_argument("--gaps", action="store_true",
                     help="test-RMSE gap to the oracle for every golden workload and format")
     args = ap.parse_args(argv)

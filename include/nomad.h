@@ -85,6 +85,20 @@ extern "C" {
                                    (default) */
 #define NOMAD_VARIANT_SIMPLE 1  /* a worker handles one token at a time */
 
+/* Epoch mode, batched kernel: how a token circulates (Sec. 3.4). */
+#define NOMAD_CIRCULATION_FLAT 0  /* every worker holding ratings of the item
+                                     once per epoch, in one keyed
+                                     pseudo-random order over all of them */
+#define NOMAD_CIRCULATION_BLOCK 1 /* the hybrid of Sec. 3.4: the token visits
+                                     all of its workers inside one thread
+                                     block (the workers of one SM) before it
+                                     moves to another block, blocks in a keyed
+                                     order; a hand-over inside a block goes
+                                     through a shared-memory inbox of the
+                                     receiving warp instead of the global
+                                     ring (the global ring when the inbox is
+                                     full) */
+
 /* Uniform mode: choice of the next worker (Alg. 1 / Sec. 3.3). */
 #define NOMAD_ROUTING_UNIFORM 0  /* uniform over all p workers (Alg. 1) */
 #define NOMAD_ROUTING_SHORTER 1  /* of two workers drawn uniformly, the one with
@@ -116,7 +130,11 @@ typedef struct nomad_schedule {
                        message); -1 = none */
   int32_t variant;  /* epoch-mode worker kernel: NOMAD_VARIANT_* */
   int32_t routing;  /* uniform mode: NOMAD_ROUTING_* */
-  int64_t reserved[5];
+  int32_t circulation; /* epoch mode, batched kernel: NOMAD_CIRCULATION_* */
+  int32_t batch_tokens; /* batched kernel: most tokens a worker takes from
+                       its queues at once, 1..16; 0 = 16 for k <= 128, 8
+                       above (larger values are capped there) */
+  int64_t reserved[4];
 } nomad_schedule;
 
 typedef struct nomad_handle nomad_t;

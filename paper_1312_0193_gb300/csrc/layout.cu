@@ -356,6 +356,55 @@ __global__ void count_flags(const uint8_t* __restrict__ flag, int64_t n,
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
+// Hybrid circulation: the segments of an item (col_segs, ordered by worker)
+// split into runs of one thread block each (blocks of wpb workers).  flag[i]
+// is 1 where position i of col_segs starts a run.
+__global__ void block_run_flags(const int32_t* __restrict__ col_segs,
+                                const int32_t* __restrict__ seg_worker,
+                                const int32_t* __restrict__ seg_col,
+                                const int32_t* __restrict__ col_seg_ptr, int64_t S, int32_t wpb,
+                                uint32_t* __restrict__ flag) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < S; i += stride) {
+    const int32_t sg = col_segs[i];
+    const bool first = i == col_seg_ptr[seg_col[sg]];
+    flag[i] = first || seg_worker[sg] / wpb != seg_worker[col_segs[i - 1]] / wpb ? 1u : 0u;
+  }
+}
+
+// Runs per item plus one (the terminal offset): run[S] = total runs.
+__global__ void block_run_counts(const int32_t* __restrict__ col_seg_ptr,
+                                 const uint32_t* __restrict__ run, int64_t n,
+                                 uint32_t* __restrict__ cnt) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += stride)
+    cnt[j] = run[col_seg_ptr[j + 1]] - run[col_seg_ptr[j]] + 1u;
+}
+
+// grp_off[col_grp_ptr[j] + g] = offset of run g of item j within its
+// segments; grp_off[col_grp_ptr[j + 1] - 1] = the item's number of segments.
+__global__ void block_run_offsets(const uint32_t* __restrict__ flag,
+                                  const uint32_t* __restrict__ run,
+                                  const int32_t* __restrict__ col_segs,
+                                  const int32_t* __restrict__ seg_col,
+                                  const int32_t* __restrict__ col_seg_ptr,
+                                  const int32_t* __restrict__ col_grp_ptr, int64_t S, int64_t n,
+                                  int32_t* __restrict__ grp_off) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < S + n; i += stride) {
+    if (i < S) {
+      if (flag[i]) {
+        const int32_t j = seg_col[col_segs[i]];
+        const int32_t a = col_seg_ptr[j];
+        grp_off[col_grp_ptr[j] + int32_t(run[i] - run[a])] = int32_t(i - a);
+      }
+    } else {
+      const int64_t j = i - S;
+      grp_off[col_grp_ptr[j + 1] - 1] = col_seg_ptr[j + 1] - col_seg_ptr[j];
+    }
+  }
+}
+
 __global__ void iota_u32(uint32_t* __restrict__ out, int64_t n) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n; s += stride)
@@ -549,6 +598,36 @@ int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
   cudaFreeAsync(ck, st); cudaFreeAsync(ck_tmp, st);
   cudaFreeAsync(cv, st); cudaFreeAsync(cv_tmp, st);
 
+  // 8b. hybrid circulation: runs of one thread block in each item's segments
+  if (h->sched.circulation == NOMAD_CIRCULATION_BLOCK) {
+    uint32_t *flag2 = nullptr, *run = nullptr, *rc = nullptr;
+    TRY(cudaMallocAsync(&flag2, sizeof(uint32_t) * salloc, st));
+    TRY(cudaMallocAsync(&run, sizeof(uint32_t) * (S + 1), st));
+    TRY(cudaMallocAsync(&rc, sizeof(uint32_t) * (n + 1), st));
+    if (S > 0) {
+      block_run_flags<<<grid_for(S), 256, 0, st>>>(h->col_segs, h->seg_worker, h->seg_col,
+                                                   h->col_seg_ptr, S, h->warps_per_block, flag2);
+      ++t_launches;
+    }
+    TRY((exclusive_scan<uint32_t, uint32_t>(flag2, run, S, run + S, st)));
+    block_run_counts<<<grid_for(n > 0 ? n : 1), 256, 0, st>>>(h->col_seg_ptr, run, n, rc);
+    ++t_launches;
+    TRY(dev_alloc(h, &vp, sizeof(int32_t) * (n + 1))); h->col_grp_ptr = (int32_t*)vp;
+    TRY((exclusive_scan<uint32_t, uint32_t>(rc, (uint32_t*)h->col_grp_ptr, n,
+                                            (uint32_t*)h->col_grp_ptr + n, st)));
+    uint32_t runs_total = 0;
+    TRY(cudaMemcpyAsync(&runs_total, h->col_grp_ptr + n, sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    TRY(dev_alloc(h, &vp, sizeof(int32_t) * (int64_t(runs_total) + 1))); h->grp_off = (int32_t*)vp;
+    block_run_offsets<<<grid_for(S + n > 0 ? S + n : 1), 256, 0, st>>>(
+        flag2, run, h->col_segs, h->seg_col, h->col_seg_ptr, h->col_grp_ptr, S, n, h->grp_off);
+    ++t_launches;
+    cudaFreeAsync(flag2, st);
+    cudaFreeAsync(run, st);
+    cudaFreeAsync(rc, st);
+  }
+
   // 9. queues: one ring per worker
   int64_t* caps = nullptr;
   TRY(cudaMallocAsync(&caps, sizeof(int64_t) * (p + 1), st));
@@ -574,7 +653,7 @@ int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
   TRY(dev_alloc(h, &vp, sizeof(int32_t) * (n + 1))); h->tok_hop = (int32_t*)vp;
   TRY(dev_alloc(h, &vp, sizeof(int32_t) * (n + 1))); h->tok_epoch = (int32_t*)vp;
   TRY(dev_alloc(h, &vp, sizeof(uint8_t) * (n + 1))); h->item_urgent = (uint8_t*)vp;
-  TRY(dev_alloc(h, &vp, sizeof(int4) * 2 * (n + 1))); h->tok_rec = (int4*)vp;
+  TRY(dev_alloc(h, &vp, sizeof(int4) * kTokRecInts * (n + 1))); h->tok_rec = (int4*)vp;
   {
     uint32_t* deg = nullptr;
     TRY(cudaMallocAsync(&deg, sizeof(uint32_t) * (n + 2), st));

@@ -54,7 +54,8 @@ void free_layout(nomad_handle* h) {
                    (void**)&h->tok_hop,    (void**)&h->tok_epoch, (void**)&h->owner,
                    (void**)&h->rec_count,  (void**)&h->log_seg,   (void**)&h->log_epoch,
                    (void**)&h->item_urgent, (void**)&h->uring,    (void**)&h->uring_tail,
-                   (void**)&h->tok_rec,    (void**)&h->ring_head};
+                   (void**)&h->tok_rec,    (void**)&h->ring_head,  (void**)&h->col_grp_ptr,
+                   (void**)&h->grp_off};
   for (void** p : ptrs) dev_free(h, p);
   h->log_cap = 0;
   h->loaded = false;
@@ -151,6 +152,7 @@ void nomad_schedule_default(nomad_schedule* s) {
   s->debug_drop_item = -1;
   s->variant = NOMAD_VARIANT_BATCHED;
   s->routing = NOMAD_ROUTING_UNIFORM;
+  s->circulation = NOMAD_CIRCULATION_FLAT;
 }
 
 const char* nomad_error_string(int32_t code) {
@@ -186,8 +188,13 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
       (sched.partition != NOMAD_PARTITION_RATINGS && sched.partition != NOMAD_PARTITION_USERS) ||
       sched.n_workers < 0 || sched.warps_per_block < 0 || sched.spin_timeout_ns < 0 ||
       (sched.variant != NOMAD_VARIANT_BATCHED && sched.variant != NOMAD_VARIANT_SIMPLE) ||
-      (sched.routing != NOMAD_ROUTING_UNIFORM && sched.routing != NOMAD_ROUTING_SHORTER))
+      (sched.routing != NOMAD_ROUTING_UNIFORM && sched.routing != NOMAD_ROUTING_SHORTER) ||
+      (sched.circulation != NOMAD_CIRCULATION_FLAT && sched.circulation != NOMAD_CIRCULATION_BLOCK) ||
+      sched.batch_tokens < 0 || sched.batch_tokens > 16)
     return NOMAD_ERR_INVALID_ARG;
+  if (sched.circulation == NOMAD_CIRCULATION_BLOCK &&
+      (sched.mode != NOMAD_MODE_EPOCH || sched.variant != NOMAD_VARIANT_BATCHED))
+    return NOMAD_ERR_UNSUPPORTED;  // the hybrid circulation: batched epoch-mode kernel only
   if (sched.precision != NOMAD_FP32 && sched.precision != NOMAD_BF16 &&
       sched.precision != NOMAD_FP8)
     return NOMAD_ERR_INVALID_ARG;
@@ -215,8 +222,9 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
   h->warps_per_block = sched.warps_per_block > 0 ? sched.warps_per_block
                                                  : default_warps_per_block();
   int bps = 0;
-  const int pmax = max_resident_workers(h->device, h->warps_per_block, h->k4, sched.precision,
-                                        sched.mode, sched.variant, &bps);
+  const int pmax = max_resident_workers(
+      h->device, h->warps_per_block, h->k4, sched.precision, sched.mode, sched.variant, &bps,
+      sched.circulation == NOMAD_CIRCULATION_BLOCK);
   if (pmax <= 0) {
     delete h;
     return NOMAD_ERR_UNSUPPORTED;

@@ -179,6 +179,10 @@ __device__ __forceinline__ float abs_max4(float4 v, float a) {
   return fmaxf(a, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
 }
 
+// int4 words of a token's next-visit record (the batched kernel; three used,
+// padded to 64 bytes so that a record never straddles a cache line)
+constexpr int kTokRecInts = 4;
+
 // ---------------------------------------------------------------- kernels
 // Status words written by device code: [0] error code (0 = ok), [1] worker,
 // [2] detail, [3] count of ownership violations (debug).
@@ -197,6 +201,14 @@ struct SgdParams {
   const int32_t* worker_seg_ptr;  // p+1
   const int32_t* col_seg_ptr;     // n+1
   const int32_t* col_segs;        // S: segments of each item, by worker
+  // hybrid circulation (NOMAD_CIRCULATION_BLOCK): item j's segments
+  // col_segs[col_seg_ptr[j] ..] fall into G_j runs of one thread block each;
+  // grp_off[col_grp_ptr[j] + g] is the offset of run g, and
+  // grp_off[col_grp_ptr[j] + G_j] = the item's number of segments
+  const int32_t* col_grp_ptr;     // n+1 (null: flat circulation)
+  const int32_t* grp_off;
+  int32_t wpb;                    // warps (workers) per thread block
+  int32_t batch_cap;              // batched kernel: tokens taken at once (0: the kernel's)
   unsigned long long* ring; // lap-tagged slots {lap:32 | segment:32}
   const int64_t* ring_base; // p
   const int32_t* ring_log2; // p: log2 of the ring capacity
@@ -278,6 +290,8 @@ struct nomad_handle {
   int32_t* worker_seg_ptr = nullptr;  // p+1
   int32_t* col_seg_ptr = nullptr;  // n+1
   int32_t* col_segs = nullptr;     // S
+  int32_t* col_grp_ptr = nullptr;  // n+1: hybrid circulation's runs per item
+  int32_t* grp_off = nullptr;      // runs + n
   // queues and tokens
   unsigned long long* ring = nullptr;
   int64_t* ring_base = nullptr;
@@ -290,7 +304,7 @@ struct nomad_handle {
   int32_t* tok_hop = nullptr;
   int32_t* tok_epoch = nullptr;
   uint8_t* item_urgent = nullptr;  // n: item degree >= half the largest
-  int4* tok_rec = nullptr;         // 2n: next-visit record of each token
+  int4* tok_rec = nullptr;         // 4n: next-visit record of each token
   float* step = nullptr;
   int32_t step_cap = 0;
   int32_t* status = nullptr;       // kStatusWords
@@ -331,11 +345,14 @@ int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
 int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t stream);
 int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cudaStream_t stream);
 int max_resident_workers(int device, int warps_per_block, int k4, int precision,
-                         int mode, int variant, int* blocks_per_sm);
+                         int mode, int variant, int* blocks_per_sm, bool blk = false);
 int default_warps_per_block();
 // Batched epoch-mode worker kernel (epoch_batched.cu): pointer and dynamic
 // shared memory per warp in bytes; nullptr for an unsupported k4.
-const void* batched_kernel(int k4, bool debug, int precision, bool many, size_t* smem_per_warp);
+const void* batched_kernel(int k4, bool debug, int precision, bool many, bool blk,
+                           size_t* smem_per_warp);
+size_t batched_inbox_bytes();   // per warp, hybrid circulation only
+size_t batched_params_bytes();  // per block, several-problem form
 
 // Initialisation, evaluation and factor copies (eval.cu).
 int init_factors(nomad_handle* h, cudaStream_t stream);

@@ -138,12 +138,23 @@ __global__ void seed_tokens(const SgdParams P, int64_t n) {
       const uint4 key = philox4x32_10(
           make_uint4(uint32_t(j), uint32_t(P.epoch0), 0u, kTagItinerary),
           make_uint2(P.seed_lo, P.seed_hi));
-      const int seg = P.col_segs[base + itinerary_slot(0u, uint32_t(d), key)];
+      int seg = P.col_segs[base + itinerary_slot(0u, uint32_t(d), key)];
       if (P.tok_rec) {  // the batched kernel: the next-visit record, item payloads
+        int4 c4 = make_int4(0, 0, 0, 0);
+        if (P.col_grp_ptr) {  // hybrid circulation: the first worker of the first run
+          const int gb = P.col_grp_ptr[j];
+          const int G = P.col_grp_ptr[j + 1] - gb - 1;
+          const int g = int(itinerary_slot(0u, uint32_t(G), key));
+          const int o = P.grp_off[gb + g];
+          const int z = P.grp_off[gb + g + 1] - o;
+          seg = P.col_segs[base + o + int(key.w % uint32_t(z))];
+          c4 = make_int4(gb, G, o, z);
+        }
         const int64_t b0 = P.seg_ptr[seg];
-        P.tok_rec[2 * j] = make_int4(seg, int(P.seg_ptr[seg + 1] - b0), int(uint32_t(b0)),
-                                     P.epoch0);
-        P.tok_rec[2 * j + 1] = make_int4(0, base, d, 0);
+        P.tok_rec[kTokRec * j] = make_int4(seg, int(P.seg_ptr[seg + 1] - b0), int(uint32_t(b0)),
+                                           P.epoch0);
+        P.tok_rec[kTokRec * j + 1] = make_int4(0, base, d, 0);
+        P.tok_rec[kTokRec * j + 2] = c4;
         if (P.use_urgent && P.item_urgent[j]) push_urgent(P, P.seg_worker[seg], uint32_t(j));
         else push_token(P, P.seg_worker[seg], uint32_t(j));
       } else {
@@ -366,11 +377,11 @@ const void* epoch_kernel_ptr(bool debug, int mode) {
 
 // The worker kernel for a handle's settings and its dynamic shared memory per
 // warp (bytes).
-const void* worker_kernel(int k4, bool debug, int mode, int variant, int precision,
+const void* worker_kernel(int k4, bool debug, int mode, int variant, int precision, bool blk,
                           size_t* smem_per_warp) {
   *smem_per_warp = 0;
   if (mode == NOMAD_MODE_EPOCH && variant == NOMAD_VARIANT_BATCHED)
-    return batched_kernel(k4, debug, precision, false, smem_per_warp);
+    return batched_kernel(k4, debug, precision, false, blk, smem_per_warp);
   if (precision != NOMAD_FP32) return nullptr;  // narrow storage: batched kernel only
   if (k4 <= 32) return epoch_kernel_ptr<1>(debug, mode);
   if (k4 <= 64) return epoch_kernel_ptr<2>(debug, mode);
@@ -379,16 +390,18 @@ const void* worker_kernel(int k4, bool debug, int mode, int variant, int precisi
 }
 
 int max_resident_workers(int device, int warps_per_block, int k4, int precision, int mode,
-                         int variant, int* blocks_per_sm) {
+                         int variant, int* blocks_per_sm, bool blk) {
+  // the hybrid circulation's inboxes follow the warps' areas
+  const size_t extra_smem_per_warp = blk ? batched_inbox_bytes() : 0;
   if (warps_per_block <= 0) warps_per_block = kDefaultWarpsPerBlock;
   if (warps_per_block > kMaxWarpsPerBlock) return -1;
   int per_sm = 1 << 30;
   // the debug variant must fit the same grid
   for (int dbg = 0; dbg < 2; ++dbg) {
     size_t spw = 0;
-    const void* fn = worker_kernel(k4, dbg, mode, variant, precision, &spw);
+    const void* fn = worker_kernel(k4, dbg, mode, variant, precision, blk, &spw);
     if (!fn) return -1;
-    const size_t smem = spw * warps_per_block;
+    const size_t smem = (spw + extra_smem_per_warp) * warps_per_block;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
             cudaSuccess)
@@ -429,6 +442,11 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
   P.worker_seg_ptr = h->worker_seg_ptr;
   P.col_seg_ptr = h->col_seg_ptr;
   P.col_segs = h->col_segs;
+  P.col_grp_ptr = (!uniform && h->sched.variant == NOMAD_VARIANT_BATCHED &&
+                   h->sched.circulation == NOMAD_CIRCULATION_BLOCK) ? h->col_grp_ptr : nullptr;
+  P.grp_off = h->grp_off;
+  P.wpb = h->warps_per_block;
+  P.batch_cap = h->sched.batch_tokens;
   P.ring = h->ring;
   P.ring_base = h->ring_base;
   P.ring_log2 = h->ring_log2;
@@ -515,8 +533,16 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
   const bool debug = h->sched.debug != 0;
   size_t spw = 0;
   const void* fn = worker_kernel(h->k4, debug, h->sched.mode, h->sched.variant,
-                                 h->sched.precision, &spw);
-  const size_t smem = spw * size_t(h->warps_per_block);
+                                 h->sched.precision, P.col_grp_ptr != nullptr, &spw);
+  // the hybrid circulation's inboxes follow the warps' areas
+  const size_t smem = (spw + (P.col_grp_ptr ? batched_inbox_bytes() : 0)) *
+                      size_t(h->warps_per_block);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+          cudaSuccess) {
+    h->last_error = "epoch: shared memory per block exceeds the device limit";
+    return NOMAD_ERR_UNSUPPORTED;
+  }
   void* args[] = {&P};
   cudaError_t e;
   cudaEventRecord(h->ev_start, st);
@@ -542,9 +568,13 @@ int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cud
   const bool debug = h0->sched.debug != 0;
   const int wpb = h0->warps_per_block;
   size_t spw = 0;
-  const void* fn = batched_kernel(h0->k4, debug, h0->sched.precision, true, &spw);
+  const void* fn = batched_kernel(h0->k4, debug, h0->sched.precision, true, false, &spw);
   if (!fn) return NOMAD_ERR_UNSUPPORTED;
-  const size_t smem = spw * size_t(wpb) + ((sizeof(SgdParams) + 15) & ~size_t(15));
+  int use_inboxes = 0;  // a problem with the hybrid circulation: inboxes after the parameters
+  for (int g = 0; g < count; ++g)
+    if (hs[g]->sched.circulation == NOMAD_CIRCULATION_BLOCK) use_inboxes = 1;
+  const size_t smem = spw * size_t(wpb) + batched_params_bytes() +
+                      (use_inboxes ? batched_inbox_bytes() * size_t(wpb) : 0);
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
           cudaSuccess) {
@@ -590,7 +620,7 @@ int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cud
     for (int g = 0; g < count; ++g) cudaEventRecord(hs[g]->ev_start, st);
     const SgdParams* aP = static_cast<const SgdParams*>(dP);
     const int2* aB = static_cast<const int2*>(dB);
-    void* args[] = {&aP, &aB};
+    void* args[] = {&aP, &aB, &use_inboxes};
     e = cudaLaunchCooperativeKernel(fn, dim3(unsigned(blocks.size())), dim3(wpb * 32), args, smem, st);
     if (!e) {
       ++h0->launches;

@@ -41,6 +41,57 @@ __device__ __forceinline__ uint32_t itinerary_slot(uint32_t hop, uint32_t d,
   return hop;  // not reached: the orbit of hop returns to [0, d)
 }
 
+// The batched kernel's record of a token's next visit, kTokRec int4 per item
+// (three used):
+// a = {segment, ratings, first record, epoch}, b = {hop, first of the
+// item's segments in col_segs, number of its segments d, gs}, c = {first run
+// of the item in grp_off, runs G, offset and size of the current run} (gs
+// and c: hybrid circulation only; gs = run hop << 16 | hop within the run).
+constexpr int kTokRec = kTokRecInts;
+
+// The visit that follows the one at flat hop `hop` (of the d per epoch) in
+// epoch e of item j: segment (-1 past the last epoch), hop, epoch and the
+// hybrid circulation's state.
+struct Route {
+  int seg, hop, epoch, gs, ro, rz;
+};
+template <bool BLK>
+__device__ __forceinline__ Route route_next(const SgdParams& P, int j, int e, int hop, int cb,
+                                            int d, int gs, int gb, int G, int ro, int rz,
+                                            int epoch_end, uint2 seed) {
+  Route r{-1, hop + 1, e, 0, 0, 0};
+  if (r.hop == d) {
+    r.hop = 0;
+    r.epoch = e + 1;
+  }
+  if (r.epoch >= epoch_end) return r;
+  const uint4 key = philox4x32_10(make_uint4(uint32_t(j), uint32_t(r.epoch), 0u, kTagItinerary),
+                                  seed);
+  if constexpr (!BLK) {  // permutation over all of the item's workers
+    r.seg = __ldg(P.col_segs + cb + itinerary_slot(uint32_t(r.hop), uint32_t(d), key));
+    return r;
+  }
+  // hybrid (Sec. 3.4): the runs of one thread block in the keyed order
+  // itinerary_slot(gh, G), the members of a run rotated by key.w
+  int gh = 0, wh = 0, o = 0, z = 0;
+  if (r.hop != 0 && (gs & 0xffff) + 1 < rz) {  // the next worker of the same run
+    gh = gs >> 16;
+    wh = (gs & 0xffff) + 1;
+    o = ro;
+    z = rz;
+  } else {  // the first worker of the next run
+    gh = r.hop == 0 ? 0 : (gs >> 16) + 1;
+    const int g = int(itinerary_slot(uint32_t(gh), uint32_t(G), key));
+    o = __ldg(P.grp_off + gb + g);
+    z = __ldg(P.grp_off + gb + g + 1) - o;
+  }
+  r.seg = __ldg(P.col_segs + cb + o + int((uint32_t(wh) + key.w) % uint32_t(z)));
+  r.gs = (gh << 16) | wh;
+  r.ro = o;
+  r.rz = z;
+  return r;
+}
+
 // Appends `payload` to worker q's ring.  The slot is written with a release
 // store: every write this thread performed or observed before it (the other
 // lanes' stores of h_j, ordered by a preceding __syncwarp) is visible to the
@@ -63,11 +114,13 @@ __device__ __forceinline__ void push_urgent(const SgdParams& P, int q, uint32_t 
 }
 
 // Lane 0 only.  Waits until worker q's ring has a token at `head` or, when
-// `uring_q` is not null, its urgent ring one at `head_u`; 0 then, -1 when the
-// wait gave up (as pop_token).  The caller reads the slots again.
+// `uring_q` is not null, its urgent ring one at `head_u`, or when `itag` is
+// not null, the shared-memory inbox slot's tag shows `iwant`; 0 then, -1 when
+// the wait gave up (as pop_token).  The caller reads the slots again.
 __device__ int wait_rings(const SgdParams& P, int q, uint32_t head, int lg,
                           const unsigned long long* ring_q, uint32_t head_u,
-                          const unsigned long long* uring_q) {
+                          const unsigned long long* uring_q, const volatile int* itag = nullptr,
+                          int iwant = 0) {
   const unsigned long long* slot = ring_q + (head & ((1u << lg) - 1u));
   const uint32_t lap = head >> lg;
   const int lgu = P.uring_log2;
@@ -79,7 +132,7 @@ __device__ int wait_rings(const SgdParams& P, int q, uint32_t head, int lg,
   unsigned ns = 32;
   for (unsigned long long it = 0; it < max_iters; ++it) {
     if (uint32_t(ld_relaxed_u64(slot) >> 32) == lap ||
-        (uslot && uint32_t(ld_relaxed_u64(uslot) >> 32) == ulap)) {
+        (uslot && uint32_t(ld_relaxed_u64(uslot) >> 32) == ulap) || (itag && *itag == iwant)) {
       fence_acq_rel_gpu();
       return 0;
     }

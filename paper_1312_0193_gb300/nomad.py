@@ -36,6 +36,8 @@ NOMAD_PARTITION_RATINGS = 0
 NOMAD_PARTITION_USERS = 1
 NOMAD_VARIANT_BATCHED = 0
 NOMAD_VARIANT_SIMPLE = 1
+NOMAD_CIRCULATION_FLAT = 0
+NOMAD_CIRCULATION_BLOCK = 1
 NOMAD_ROUTING_UNIFORM = 0
 NOMAD_ROUTING_SHORTER = 1
 NOMAD_COO = 0
@@ -50,7 +52,8 @@ class nomad_schedule(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("spin_timeout_ns", ctypes.c_int64),
                 ("device", ctypes.c_int32), ("debug_drop_item", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("routing", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 5)]
+                ("circulation", ctypes.c_int32), ("batch_tokens", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 class nomad_info(ctypes.Structure):
@@ -229,7 +232,8 @@ class Nomad:
     def __init__(self, m, n, k, lam, alpha=0.012, beta=0.05, mode="epoch",
                  precision="fp32", partition="ratings", n_workers=0,
                  warps_per_block=0, debug=False, seed=1, spin_timeout_ns=0,
-                 device=0, debug_drop_item=-1, variant="batched", routing="uniform"):
+                 device=0, debug_drop_item=-1, variant="batched", routing="uniform",
+                 circulation="flat", batch_tokens=0):
         s = nomad_schedule_default()
         s.alpha, s.beta = alpha, beta
         s.mode = {"epoch": NOMAD_MODE_EPOCH, "uniform": NOMAD_MODE_UNIFORM}[mode]
@@ -245,6 +249,9 @@ class Nomad:
         s.debug_drop_item = debug_drop_item
         s.variant = {"batched": NOMAD_VARIANT_BATCHED, "simple": NOMAD_VARIANT_SIMPLE}[variant]
         s.routing = {"uniform": NOMAD_ROUTING_UNIFORM, "shorter": NOMAD_ROUTING_SHORTER}[routing]
+        s.circulation = {"flat": NOMAD_CIRCULATION_FLAT,
+                         "block": NOMAD_CIRCULATION_BLOCK}[circulation]
+        s.batch_tokens = batch_tokens
         self.schedule = s
         self.m, self.n, self.k, self.lam = m, n, k, lam
         self.h = nomad_create(m, n, k, lam, s)

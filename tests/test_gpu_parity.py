@@ -348,3 +348,54 @@ def test_uniform_mode_replay_and_budget(tiny, p, routing):
     assert rel(Wg, Wo) < REPLAY_TOL and rel(Hg, Ho) < REPLAY_TOL
     assert row_rel_max(Wg, Wo) < ROW_TOL and row_rel_max(Hg, Ho) < ROW_TOL
     assert seg.size > 5 * p  # many visits, some of them to workers without ratings
+
+
+# ---------------------------------------------------------------- hybrid circulation
+@pytest.mark.parametrize("p,k,epochs,calls", [(64, 10, 3, 2), (16, 100, 2, 1), (64, 100, 2, 1)])
+def test_block_circulation_replay(p, k, epochs, calls):
+    """The hybrid circulation of Sec. 3.4 (a token visits all of its workers
+    in one thread block, handed over through shared-memory inboxes, before
+    it moves to another block): every segment once per epoch, replay parity
+    as for the flat circulation, and in every epoch each item's visits come
+    in one contiguous run per block."""
+    r = synth.tiny_planted(1) if k == 10 else synth.netflix_shaped(0.002, seed=13)
+    replay_check(r, k, 0.05, 0.01, 0.05, epochs, p=p, calls=calls, circulation="block")
+    # the run structure, from one more debug run's log
+    with make(r, k, 0.05, alpha=0.01, beta=0.05, debug=True, n_workers=p,
+              circulation="block") as nm:
+        L, _ = oracle_layout(nm, r)
+        wpb = nm.info()["warps_per_block"]
+        nm.epoch(epochs)
+        nm.check()
+        seg, ep = nm.replay_log()
+    blocks = L["seg_worker"][seg] // wpb
+    items = L["seg_col"][seg]
+    for e in range(epochs):
+        for j in np.unique(items[ep == e])[:200]:
+            b = blocks[(ep == e) & (items == j)]
+            changes = np.flatnonzero(np.diff(b) != 0)
+            # a block, once left, is not visited again in the epoch
+            runs = np.concatenate([b[:1], b[changes + 1]])
+            assert np.unique(runs).size == runs.size, (j, e, b)
+
+
+def test_block_circulation_free_run_matches_oracle_rmse(tiny):
+    """Non-debug run with the hybrid circulation, 20 epochs at the paper's
+    schedule: test RMSE within 0.5% of the binary64 oracle's serial NOMAD."""
+    tr, tc, tv, er, ec, ev = tiny.numpy()
+    with make(tiny, 10, 0.05, alpha=0.012, beta=0.05, circulation="block") as nm:
+        W0, H0 = nm.factors()
+        nm.epoch(20)
+        g = nm.rmse(er, ec, ev)
+        L, _ = oracle_layout(nm, tiny)
+    Wo, Ho, _, _ = oracle.serial_nomad(L, W0, H0, 0.05, 0.012, 0.05, 20, 9)
+    o = oracle.rmse(er, ec, ev, Wo, Ho)
+    assert abs(g - o) <= 0.005 * o, (g, o)
+
+
+def test_block_circulation_only_batched_epoch():
+    with pytest.raises(NomadError) as e:
+        Nomad(10, 10, 4, 0.1, circulation="block", variant="simple")
+    assert e.value.code == nb.NOMAD_ERR_UNSUPPORTED
+    with pytest.raises(NomadError):
+        Nomad(10, 10, 4, 0.1, circulation="block", mode="uniform")
