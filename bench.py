@@ -301,6 +301,7 @@ def run_ours(args):
     achieved_gbs = nnz * bytes_per_update / kern_avg_s / 1e9
     peak, peak_src = load_peaks()
     traffic = None
+    l2_hit = None
     tr_path = os.path.join(ROOT, "profiles", "epoch_kernel_traffic.json")
     if os.path.exists(tr_path):
         try:
@@ -310,8 +311,11 @@ def run_ours(args):
                     and tj.get("precision", "fp32") == args.precision
                     and tj.get("kernel_rev") == kernel_rev()):
                 traffic = tj.get("dram_bytes_per_launch")
+                if "l2_sector_hit_rate_pct" in tj:
+                    l2_hit = {"pct": tj["l2_sector_hit_rate_pct"],
+                              "case": tj.get("l2_hit_rate_case", "")}
         except Exception:
-            traffic = None
+            traffic = l2_hit = None
 
     ttt = None
     if rank == 0 and world == 1 and not args.no_ttt:
@@ -355,7 +359,8 @@ def run_ours(args):
                          if peak_src == "measured" else "fallback 6.8 TB/s",
                          "kernel": "nomad_batched_kernel" if args.mode == "epoch" else
                                    "nomad_uniform_kernel", "kernel_ms": kern_avg_s * 1e3,
-                         "bytes_per_update": bytes_per_update},
+                         "bytes_per_update": bytes_per_update,
+                         "l2_hit_rate": l2_hit},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_units / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,

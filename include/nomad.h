@@ -134,7 +134,15 @@ typedef struct nomad_schedule {
   int32_t batch_tokens; /* batched kernel: most tokens a worker takes from
                        its queues at once, 1..16; 0 = 16 for k <= 128, 8
                        above (larger values are capped there) */
-  int64_t reserved[4];
+  int32_t epochs_per_launch; /* epoch mode: 0 or 1 = one kernel launch per
+                       epoch, so every token finishes epoch e before any
+                       token starts e+1 (the epochs of the permutation
+                       circulation, Sec. 3.4, stay in step; the default);
+                       n > 1 = up to n epochs in one launch, tokens free to
+                       run epochs ahead of each other (no end-of-epoch wait,
+                       but the descent per epoch is slower on skewed data) */
+  int32_t reserved32;
+  int64_t reserved[3];
 } nomad_schedule;
 
 typedef struct nomad_handle nomad_t;
@@ -183,10 +191,11 @@ NOMAD_API int nomad_load_ratings(nomad_t *h, int32_t fmt, int64_t nnz, const voi
                        const int32_t *minor, const float *vals,
                        int32_t device_ptrs, void *stream);
 
-/* Run n_epochs epochs of NOMAD (Alg. 1) in one persistent launch: every
- * worker pops item tokens from its queue, applies the SGD updates of
- * Eq. w_update / h_update to its ratings of that item, and hands the token
- * on.  In NOMAD_MODE_EPOCH every rating is updated exactly once per epoch.
+/* Run n_epochs epochs of NOMAD (Alg. 1) in persistent launches (one per
+ * epoch, or schedule.epochs_per_launch epochs each): every worker pops item
+ * tokens from its queue, applies the SGD updates of Eq. w_update / h_update
+ * to its ratings of that item, and hands the token on.  In NOMAD_MODE_EPOCH
+ * every rating is updated exactly once per epoch.
  * Asynchronous on `stream`; errors raised on the device (timeout, ownership)
  * are reported by the next nomad_check / nomad_rmse / nomad_objective /
  * nomad_get_factors call. */

@@ -275,6 +275,24 @@ __device__ __forceinline__ void cp_chunk(T* smem, const T* gmem) {
   else if constexpr (sizeof(T) == 8) cp_async8(smem, gmem);
   else cp_async4(smem, gmem);
 }
+// cp_chunk under a predicate, without a branch (so that it can be scheduled
+// among independent instructions); nothing is read when `pred` is false
+template <typename T>
+__device__ __forceinline__ void cp_chunk_if(bool pred, T* smem, const T* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  if constexpr (sizeof(T) == 16)
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t"
+                 "@p cp.async.cg.shared.global [%0], [%1], 16;\n\t}\n" ::"r"(sa), "l"(gmem),
+                 "r"(int(pred)) : "memory");
+  else if constexpr (sizeof(T) == 8)
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t"
+                 "@p cp.async.ca.shared.global [%0], [%1], 8;\n\t}\n" ::"r"(sa), "l"(gmem),
+                 "r"(int(pred)) : "memory");
+  else
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t"
+                 "@p cp.async.ca.shared.global [%0], [%1], 4;\n\t}\n" ::"r"(sa), "l"(gmem),
+                 "r"(int(pred)) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -1067,20 +1085,14 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
         load_records<kBatch>(recs, P.rec, v_soff, v_beg, nb, loaded, cnt, lane);
         loaded += cnt;
       }
-      const int pp = t + R - 1;
-      if (pp < T) {
-        prefetch(pp, nrow);
-      } else if (lane == pp % R) {
-        win = -1;
-        fwd = -1;
-      }
-      cp_commit();
-      cp_wait<R - 1>();
+      // position t's row was copied R-1 ticks ago; the copy of position
+      // t + R - 1 (issued below, after t's slot is read) is not committed
+      // yet, so R-2 younger groups may still be in flight
+      cp_wait<R - 2>();
       __syncwarp();
 
-      const int2 rc = recs[t % kRecBuf];
-      const int slot = t % R;
-      const int fslot = __shfl_sync(kFull, fwd, slot);  // a later position's slot, or -1
+      const int2 rc = recs[unsigned(t) % kRecBuf];
+      const int slot = int(unsigned(t) % R);
       w_t* wrow = W4 + int64_t(rc.x) * pitch4;
       const float sc = PR == kFP8 ? rsc[slot] : 1.f;
       float4 w[CPL];
@@ -1098,7 +1110,39 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) acc = dot4_acc(w[cc], h[cc], acc);
-      const float err = __int_as_float(rc.y) - warp_sum(acc.x + acc.y);
+      float dsum = acc.x + acc.y;
+      dsum += __shfl_xor_sync(kFull, dsum, 16);
+      {  // the copy of position pp = t + R - 1 into the slot t - 1 left, decided
+         // and issued without branches while the reduction's shuffles are in
+         // flight; its row (nrow) was read from the records a tick ahead
+        const int pp = t + R - 1;
+        const bool live = pp < T;
+        const int pslot = int(unsigned(pp) % R);
+        const unsigned m = __ballot_sync(kFull, live && lane < R && lane != pslot && win == nrow);
+        // the latest position in flight with that row: going back from pp - 1
+        // the slots are pslot - 1, ..., 0, R - 1, ..., pslot + 1; it writes
+        // its updated row into pslot as well
+        const unsigned mm = (m | (m << R)) & ((1u << (pslot + R)) - 1u);
+        const int tgt = m ? int(unsigned(31 - __clz(mm)) % R) : -1;
+        const bool copy = live && m == 0u;
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+          const int idx = lane + 32 * cc;
+          cp_chunk_if(copy && idx < k4, rows + (pslot * CPL + cc) * 32 + lane,
+                      W4 + int64_t(nrow) * pitch4 + idx);
+        }
+        if constexpr (PR == kFP8) cp_chunk_if(copy && lane == 0, rsc + pslot, Wscale + nrow);
+        fwd = lane == tgt ? pslot : fwd;
+        win = lane == pslot ? (live ? nrow : -1) : win;
+        fwd = lane == pslot ? -1 : fwd;
+        cp_commit();
+      }
+      dsum += __shfl_xor_sync(kFull, dsum, 8);
+      dsum += __shfl_xor_sync(kFull, dsum, 4);
+      dsum += __shfl_xor_sync(kFull, dsum, 2);
+      dsum += __shfl_xor_sync(kFull, dsum, 1);
+      const int fslot = __shfl_sync(kFull, fwd, slot);  // a later position's slot, or -1
+      const float err = __int_as_float(rc.y) - dsum;
       const float se = s * err;
       const float2 se2 = make_float2(se, se);
       float4 wn[CPL];

@@ -190,7 +190,7 @@ int nomad_create(int64_t m, int64_t n, int32_t k, float lambda, const nomad_sche
       (sched.variant != NOMAD_VARIANT_BATCHED && sched.variant != NOMAD_VARIANT_SIMPLE) ||
       (sched.routing != NOMAD_ROUTING_UNIFORM && sched.routing != NOMAD_ROUTING_SHORTER) ||
       (sched.circulation != NOMAD_CIRCULATION_FLAT && sched.circulation != NOMAD_CIRCULATION_BLOCK) ||
-      sched.batch_tokens < 0 || sched.batch_tokens > 16)
+      sched.batch_tokens < 0 || sched.batch_tokens > 16 || sched.epochs_per_launch < 0)
     return NOMAD_ERR_INVALID_ARG;
   if (sched.circulation == NOMAD_CIRCULATION_BLOCK &&
       (sched.mode != NOMAD_MODE_EPOCH || sched.variant != NOMAD_VARIANT_BATCHED))

@@ -425,7 +425,8 @@ namespace {
 // The worker kernel's parameters for the next n_epochs of handle h (in *out),
 // after the launch's preparation on `st`: ring, queue and status resets, the
 // step-size table and the initial tokens.
-int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams* out) {
+int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams* out,
+                   int32_t epoch_off = 0, bool first = true) {
   const bool uniform = h->sched.mode == NOMAD_MODE_UNIFORM;
   const bool debug = h->sched.debug != 0;
   SgdParams& P = *out;
@@ -464,7 +465,7 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
   P.use_urgent = (!uniform && h->sched.variant == NOMAD_VARIANT_BATCHED && h->k4 <= 32 &&
                   h->uring != nullptr) ? 1 : 0;
   P.step = h->step;
-  P.epoch0 = int32_t(h->epochs_done);
+  P.epoch0 = int32_t(h->epochs_done) + epoch_off;
   P.n_epochs = n_epochs;
   P.p = h->p;
   P.lambda = h->lambda;
@@ -494,9 +495,12 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
                                         sizeof(unsigned long long) * (int64_t(h->p) << h->uring_log2),
                                         st))) ||
       (h->uring_tail && (e = cudaMemsetAsync(h->uring_tail, 0, sizeof(uint32_t) * h->p, st))) ||
-      (e = cudaMemsetAsync(h->status, 0, sizeof(int32_t) * kStatusWords, st)) ||
-      (e = cudaMemsetAsync(h->span, 0xff, sizeof(unsigned long long), st)) ||
-      (e = cudaMemsetAsync(h->span + 1, 0, sizeof(unsigned long long), st))) {
+      // status and span cover the whole call: an error of one launch stays
+      // for nomad_check (the call's later launches see it and stop at their
+      // first wait), and the span runs from the first launch's start
+      (first && (e = cudaMemsetAsync(h->status, 0, sizeof(int32_t) * kStatusWords, st))) ||
+      (first && (e = cudaMemsetAsync(h->span, 0xff, sizeof(unsigned long long), st))) ||
+      (first && (e = cudaMemsetAsync(h->span + 1, 0, sizeof(unsigned long long), st)))) {
     h->last_error = std::string("epoch: ") + cudaGetErrorString(e);
     return NOMAD_ERR_CUDA;
   }
@@ -508,7 +512,7 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
                                        h->sched.beta);
     ++h->launches;
   }
-  if (debug) cudaMemsetAsync(h->log_ticket, 0, sizeof(uint32_t), st);
+  if (debug && first) cudaMemsetAsync(h->log_ticket, 0, sizeof(uint32_t), st);
   const int64_t n = h->n;
   unsigned seed_grid = unsigned((n + 255) / 256);
   if (seed_grid < 1) seed_grid = 1;
@@ -526,33 +530,44 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
 
 }  // namespace
 
+// Epochs per launch of a call: one (the epochs kept in step), or the
+// schedule's epochs_per_launch; uniform mode runs a call in one launch.
+int32_t epochs_per_launch(const nomad_handle* h, int32_t n_epochs) {
+  if (h->sched.mode == NOMAD_MODE_UNIFORM) return n_epochs;
+  const int32_t e = h->sched.epochs_per_launch > 1 ? h->sched.epochs_per_launch : 1;
+  return e < n_epochs ? e : n_epochs;
+}
+
 int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
-  SgdParams P{};
-  const int rc = prepare_epochs(h, n_epochs, st, &P);
-  if (rc != NOMAD_OK || h->nnz == 0) return rc;
-  const bool debug = h->sched.debug != 0;
-  size_t spw = 0;
-  const void* fn = worker_kernel(h->k4, debug, h->sched.mode, h->sched.variant,
-                                 h->sched.precision, P.col_grp_ptr != nullptr, &spw);
-  // the hybrid circulation's inboxes follow the warps' areas
-  const size_t smem = (spw + (P.col_grp_ptr ? batched_inbox_bytes() : 0)) *
-                      size_t(h->warps_per_block);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-          cudaSuccess) {
-    h->last_error = "epoch: shared memory per block exceeds the device limit";
-    return NOMAD_ERR_UNSUPPORTED;
+  const int32_t per = epochs_per_launch(h, n_epochs);
+  for (int32_t done = 0; done < n_epochs; done += per) {
+    const int32_t ne = n_epochs - done < per ? n_epochs - done : per;
+    SgdParams P{};
+    const int rc = prepare_epochs(h, ne, st, &P, done, done == 0);
+    if (rc != NOMAD_OK || h->nnz == 0) return rc;
+    const bool debug = h->sched.debug != 0;
+    size_t spw = 0;
+    const void* fn = worker_kernel(h->k4, debug, h->sched.mode, h->sched.variant,
+                                   h->sched.precision, P.col_grp_ptr != nullptr, &spw);
+    // the hybrid circulation's inboxes follow the warps' areas
+    const size_t smem = (spw + (P.col_grp_ptr ? batched_inbox_bytes() : 0)) *
+                        size_t(h->warps_per_block);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+            cudaSuccess) {
+      h->last_error = "epoch: shared memory per block exceeds the device limit";
+      return NOMAD_ERR_UNSUPPORTED;
+    }
+    void* args[] = {&P};
+    if (done == 0) cudaEventRecord(h->ev_start, st);
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(h->blocks),
+                                                      dim3(h->warps_per_block * 32), args, smem, st);
+    if (e != cudaSuccess) {
+      h->last_error = std::string("epoch: cooperative launch: ") + cudaGetErrorString(e);
+      return NOMAD_ERR_CUDA;
+    }
+    ++h->launches;
   }
-  void* args[] = {&P};
-  cudaError_t e;
-  cudaEventRecord(h->ev_start, st);
-  e = cudaLaunchCooperativeKernel(fn, dim3(h->blocks), dim3(h->warps_per_block * 32), args,
-                                  smem, st);
-  if (e != cudaSuccess) {
-    h->last_error = std::string("epoch: cooperative launch: ") + cudaGetErrorString(e);
-    return NOMAD_ERR_CUDA;
-  }
-  ++h->launches;
   cudaEventRecord(h->ev_stop, st);
   h->ev_recorded = true;
   return NOMAD_OK;
@@ -595,46 +610,50 @@ int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cud
                      std::to_string(int64_t(per_sm) * sms) + ")";
     return NOMAD_ERR_UNSUPPORTED;
   }
-  std::vector<SgdParams> Ps;
-  std::vector<int2> blocks;
-  Ps.reserve(size_t(count));
-  for (int g = 0; g < count; ++g) {
-    SgdParams P{};
-    const int rc = prepare_epochs(hs[g], n_epochs, st, &P);
-    if (rc != NOMAD_OK) {
-      if (hs[g] != h0) h0->last_error = hs[g]->last_error;
-      return rc;
-    }
-    if (hs[g]->nnz == 0) continue;
-    for (int b = 0; b < hs[g]->blocks; ++b) blocks.push_back(make_int2(int(Ps.size()), b));
-    Ps.push_back(P);
-  }
-  if (blocks.empty()) return NOMAD_OK;
-  void* dP = nullptr;
-  void* dB = nullptr;
-  cudaError_t e = cudaMallocAsync(&dP, sizeof(SgdParams) * Ps.size(), st);
-  if (!e) e = cudaMallocAsync(&dB, sizeof(int2) * blocks.size(), st);
-  if (!e) e = cudaMemcpyAsync(dP, Ps.data(), sizeof(SgdParams) * Ps.size(), cudaMemcpyHostToDevice, st);
-  if (!e) e = cudaMemcpyAsync(dB, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice, st);
-  if (!e) {
-    for (int g = 0; g < count; ++g) cudaEventRecord(hs[g]->ev_start, st);
-    const SgdParams* aP = static_cast<const SgdParams*>(dP);
-    const int2* aB = static_cast<const int2*>(dB);
-    void* args[] = {&aP, &aB, &use_inboxes};
-    e = cudaLaunchCooperativeKernel(fn, dim3(unsigned(blocks.size())), dim3(wpb * 32), args, smem, st);
-    if (!e) {
-      ++h0->launches;
-      for (int g = 0; g < count; ++g) {
-        cudaEventRecord(hs[g]->ev_stop, st);
-        hs[g]->ev_recorded = true;
+  // one launch per epoch (or the first handle's epochs_per_launch)
+  const int32_t per = epochs_per_launch(h0, n_epochs);
+  for (int32_t done = 0; done < n_epochs; done += per) {
+    const int32_t ne = n_epochs - done < per ? n_epochs - done : per;
+    std::vector<SgdParams> Ps;
+    std::vector<int2> blocks;
+    Ps.reserve(size_t(count));
+    for (int g = 0; g < count; ++g) {
+      SgdParams P{};
+      const int rc = prepare_epochs(hs[g], ne, st, &P, done, done == 0);
+      if (rc != NOMAD_OK) {
+        if (hs[g] != h0) h0->last_error = hs[g]->last_error;
+        return rc;
       }
+      if (hs[g]->nnz == 0) continue;
+      for (int b = 0; b < hs[g]->blocks; ++b) blocks.push_back(make_int2(int(Ps.size()), b));
+      Ps.push_back(P);
+    }
+    if (blocks.empty()) return NOMAD_OK;
+    void* dP = nullptr;
+    void* dB = nullptr;
+    cudaError_t e = cudaMallocAsync(&dP, sizeof(SgdParams) * Ps.size(), st);
+    if (!e) e = cudaMallocAsync(&dB, sizeof(int2) * blocks.size(), st);
+    if (!e) e = cudaMemcpyAsync(dP, Ps.data(), sizeof(SgdParams) * Ps.size(), cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(dB, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice, st);
+    if (!e) {
+      if (done == 0)
+        for (int g = 0; g < count; ++g) cudaEventRecord(hs[g]->ev_start, st);
+      const SgdParams* aP = static_cast<const SgdParams*>(dP);
+      const int2* aB = static_cast<const int2*>(dB);
+      void* args[] = {&aP, &aB, &use_inboxes};
+      e = cudaLaunchCooperativeKernel(fn, dim3(unsigned(blocks.size())), dim3(wpb * 32), args, smem, st);
+      if (!e) ++h0->launches;
+    }
+    if (dP) cudaFreeAsync(dP, st);
+    if (dB) cudaFreeAsync(dB, st);
+    if (e != cudaSuccess) {
+      h0->last_error = std::string("epoch_many: ") + cudaGetErrorString(e);
+      return NOMAD_ERR_CUDA;
     }
   }
-  if (dP) cudaFreeAsync(dP, st);
-  if (dB) cudaFreeAsync(dB, st);
-  if (e != cudaSuccess) {
-    h0->last_error = std::string("epoch_many: ") + cudaGetErrorString(e);
-    return NOMAD_ERR_CUDA;
+  for (int g = 0; g < count; ++g) {
+    cudaEventRecord(hs[g]->ev_stop, st);
+    hs[g]->ev_recorded = true;
   }
   return NOMAD_OK;
 }

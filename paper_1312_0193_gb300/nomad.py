@@ -53,7 +53,8 @@ class nomad_schedule(ctypes.Structure):
                 ("device", ctypes.c_int32), ("debug_drop_item", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("routing", ctypes.c_int32),
                 ("circulation", ctypes.c_int32), ("batch_tokens", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("epochs_per_launch", ctypes.c_int32), ("reserved32", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 3)]
 
 
 class nomad_info(ctypes.Structure):
@@ -233,7 +234,7 @@ class Nomad:
                  precision="fp32", partition="ratings", n_workers=0,
                  warps_per_block=0, debug=False, seed=1, spin_timeout_ns=0,
                  device=0, debug_drop_item=-1, variant="batched", routing="uniform",
-                 circulation="flat", batch_tokens=0):
+                 circulation="flat", batch_tokens=0, epochs_per_launch=0):
         s = nomad_schedule_default()
         s.alpha, s.beta = alpha, beta
         s.mode = {"epoch": NOMAD_MODE_EPOCH, "uniform": NOMAD_MODE_UNIFORM}[mode]
@@ -252,6 +253,7 @@ class Nomad:
         s.circulation = {"flat": NOMAD_CIRCULATION_FLAT,
                          "block": NOMAD_CIRCULATION_BLOCK}[circulation]
         s.batch_tokens = batch_tokens
+        s.epochs_per_launch = epochs_per_launch
         self.schedule = s
         self.m, self.n, self.k, self.lam = m, n, k, lam
         self.h = nomad_create(m, n, k, lam, s)

@@ -280,6 +280,29 @@ def test_lost_token_times_out_and_recovers(tiny):
         nm.check()  # cleared
 
 
+def test_lost_token_error_kept_across_a_calls_launches(tiny):
+    """Several epochs run as one launch per epoch: the first launch's timeout
+    stays in the status word (a later launch of the same call does not clear
+    it), and the later launches stop at their first wait instead of waiting
+    out their own timeouts."""
+    import time
+    item = int(tiny.train_cols[0])
+    timeout_ns = 300_000_000
+    with make(tiny, 10, 0.05, n_workers=16, spin_timeout_ns=timeout_ns,
+              debug_drop_item=item, epochs_per_launch=1) as nm:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nm.epoch(4)
+        with pytest.raises(NomadError) as e:
+            nm.check()
+        dt = time.perf_counter() - t0
+        assert e.value.code == nb.NOMAD_ERR_TIMEOUT
+        assert nm.info()["kernel_launches"] >= 4
+        # one timeout, not four
+        assert dt < 2.5 * timeout_ns * 1e-9, dt
+        nm.check()
+
+
 # ---------------------------------------------------------------- free run
 def test_free_run_matches_oracle_rmse(tiny):
     """Non-debug run of 20 epochs at the paper's schedule (alpha 0.012,
