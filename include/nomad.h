@@ -93,11 +93,12 @@ extern "C" {
                                      all of its workers inside one thread
                                      block (the workers of one SM) before it
                                      moves to another block, blocks in a keyed
-                                     order; a hand-over inside a block goes
-                                     through a shared-memory inbox of the
-                                     receiving warp instead of the global
-                                     ring (the global ring when the inbox is
-                                     full) */
+                                     order and the workers of a block in a
+                                     second keyed order; a hand-over inside a
+                                     block goes through a shared-memory inbox
+                                     of the receiving warp instead of the
+                                     global ring (the global ring when the
+                                     inbox is full) */
 
 /* Uniform mode: choice of the next worker (Alg. 1 / Sec. 3.3). */
 #define NOMAD_ROUTING_UNIFORM 0  /* uniform over all p workers (Alg. 1) */

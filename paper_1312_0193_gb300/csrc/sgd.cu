@@ -147,7 +147,8 @@ __global__ void seed_tokens(const SgdParams P, int64_t n) {
           const int g = int(itinerary_slot(0u, uint32_t(G), key));
           const int o = P.grp_off[gb + g];
           const int z = P.grp_off[gb + g + 1] - o;
-          seg = P.col_segs[base + o + int(key.w % uint32_t(z))];
+          seg = P.col_segs[base + o + int(itinerary_slot(
+                                         0u, uint32_t(z), make_uint4(key.w, key.z, key.y, key.x)))];
           c4 = make_int4(gb, G, o, z);
         }
         const int64_t b0 = P.seg_ptr[seg];

@@ -72,7 +72,8 @@ __device__ __forceinline__ Route route_next(const SgdParams& P, int j, int e, in
     return r;
   }
   // hybrid (Sec. 3.4): the runs of one thread block in the keyed order
-  // itinerary_slot(gh, G), the members of a run rotated by key.w
+  // itinerary_slot(gh, G); within a run, its workers in a second keyed
+  // permutation (the key's words reversed)
   int gh = 0, wh = 0, o = 0, z = 0;
   if (r.hop != 0 && (gs & 0xffff) + 1 < rz) {  // the next worker of the same run
     gh = gs >> 16;
@@ -85,7 +86,8 @@ __device__ __forceinline__ Route route_next(const SgdParams& P, int j, int e, in
     o = __ldg(P.grp_off + gb + g);
     z = __ldg(P.grp_off + gb + g + 1) - o;
   }
-  r.seg = __ldg(P.col_segs + cb + o + int((uint32_t(wh) + key.w) % uint32_t(z)));
+  const uint4 kin = make_uint4(key.w, key.z, key.y, key.x);
+  r.seg = __ldg(P.col_segs + cb + o + int(itinerary_slot(uint32_t(wh), uint32_t(z), kin)));
   r.gs = (gh << 16) | wh;
   r.ro = o;
   r.rz = z;
