@@ -525,6 +525,51 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Fmt<PR>::w
     if constexpr (PR != kF32) __syncwarp();  // the bits drawn above are visible
     // vector updates in rating order
     const int nu = c - b * B < B ? c - b * B : B;
+    if constexpr (PR == kFP8) {
+      // E4M3: the block's updated rows first (the chain through h), then
+      // their scales from one interleaved max-reduction of the B rows, so
+      // that the B reductions and divisions overlap instead of each
+      // waiting for the one before
+      float4 wn[B][CPL];
+      float am[B];
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        const float se = s * e[i];
+        const float2 se2 = make_float2(se, se);
+        am[i] = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+          if (i < nu) {
+            wn[i][cc] = axpby(al2, w[i][cc], se2, h[cc]);  // a w_u + s e_u h_u
+            h[cc] = axpby(se2, w[i][cc], al2, h[cc]);      // a h_u + s e_u w_u
+          } else {
+            wn[i][cc] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          am[i] = abs_max4(wn[i][cc], am[i]);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < B; ++i) am[i] = fmaxf(am[i], __shfl_xor_sync(kFull, am[i], o));
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        if (i >= nu) break;
+        const int u = b * B + i;
+        const int row = row_at(u);
+        w_t* wrow = W4 + int64_t(row) * pitch4;
+        float sc, g;
+        e4m3_row_scale(am[i], &sc, &g);
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+          const uint2 rb = rbuf[i * CPL * 32 + lane + 32 * cc];
+          if (lane + 32 * cc < k4) wrow[lane + 32 * cc] = e4m3_pack(wn[i][cc], g, true, rb.x, rb.y);
+        }
+        if (lane == 0) Wscale[row] = sc;
+        if (DEBUG && lane == 0) rec_count[beg + u] += 1;
+      }
+      continue;
+    }
 #pragma unroll
     for (int i = 0; i < B; ++i) {
       if (i >= nu) break;

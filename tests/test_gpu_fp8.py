@@ -37,7 +37,8 @@ it is exact and where the drift has not begun:
    along a chain of hundreds of ratings h then drifts by about 1e-3 relative
    (measured 1.8e-3), so a later rounding differs with probability about
    8 x 1e-3 per entry write and its flips cascade: up to 25% of the entries
-   may be flipped there (measured 15%).
+   may be flipped there (measured from 0.03% to 15% over five runs: how far
+   the flips spread depends on the free-run order).
 """
 import numpy as np
 import pytest
