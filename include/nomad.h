@@ -164,7 +164,9 @@ typedef struct nomad_info {
   int32_t sm_count;
   int64_t device_bytes;    /* device memory held by the handle */
   int64_t kernel_launches; /* kernels launched by the handle so far */
-  int64_t reserved[3];
+  int64_t predrawn_ratings; /* ratings whose W rounding bits are drawn before
+                               each launch (see nomad_load_ratings); 0 = none */
+  int64_t reserved[2];
 } nomad_info;
 
 /* Library defaults: alpha 0.012, beta 0.05 (Table 1, Netflix), epoch mode,
@@ -187,7 +189,15 @@ NOMAD_API int nomad_create(int64_t m, int64_t n, int32_t k, float lambda,
  *  vals = const float[nnz].
  * Errors: NOMAD_ERR_RANGE (index out of range), NOMAD_ERR_DUP_ENTRY.
  * Synchronises with the device before returning.  May be called again to
- * replace the ratings (the factors are kept). */
+ * replace the ratings (the factors are kept).
+ * With NOMAD_BF16 or NOMAD_FP8 storage (batched kernel, epoch mode, k <=
+ * 128) it may also reserve 8 ceil(k/4) bytes per rating of the items with
+ * the most ratings (at least half the largest item degree): their W
+ * rounding bits are then drawn there before each one-epoch launch, off the
+ * chains of visits of those items.  Only when those ratings are at most a
+ * quarter of all and the reservation fits in a quarter of the free device
+ * memory and 32 GiB; otherwise the kernel draws the bits itself.
+ * nomad_get_info's device_bytes includes the reservation. */
 NOMAD_API int nomad_load_ratings(nomad_t *h, int32_t fmt, int64_t nnz, const void *major,
                        const int32_t *minor, const float *vals,
                        int32_t device_ptrs, void *stream);

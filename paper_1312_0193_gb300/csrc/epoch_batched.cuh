@@ -385,18 +385,35 @@ __device__ __forceinline__ float warp_sum_transposed(float (&v)[32], int lane) {
 // row.  Records are held in lane registers, three 32-record chunks (lane i
 // holds record i of a chunk).  Earlier stores of this warp precede these
 // loads in program order.
-template <int CPL, int PR, bool DEBUG, int NCH>
+//
+// Narrow formats: the rounding bits of a block are drawn into `rbuf` while
+// the block's products are reduced, or, with PRE, read from `pre` (drawn
+// before the launch, record u of the visit at pre + u * k4): copied with the
+// block's rows into `pbuf` (LB + 1 blocks of B records, each lane its own
+// chunks), which takes the draws off the chain of the visit.
+template <int CPL>
+__host__ __device__ constexpr int long_visit_b() {
+  return CPL == 4 ? 4 : 7;
+}
+// blocks of rows in flight; positions up to B*(b + LB) + B - 1 must lie in
+// record chunks c0 and c0 + 1
+template <int CPL, int NCH>
+__host__ __device__ constexpr int long_visit_lb() {
+  constexpr int B = long_visit_b<CPL>();
+  return (NCH / CPL) / B < 33 / B - 1 ? (NCH / CPL) / B : 33 / B - 1;
+}
+
+template <int CPL, int PR, bool DEBUG, int NCH, bool PRE = false>
 __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Fmt<PR>::w_t* rows, float* rsc,
                                            uint2* rbuf, typename Fmt<PR>::w_t* W4, float* Wscale,
                                            int64_t pitch4, int k4, const int2* __restrict__ rec,
                                            int64_t beg, int c, float s, float lam, int epoch,
-                                           uint2 seed, int lane, int32_t* rec_count) {
-  constexpr int B = CPL == 4 ? 4 : 7;
+                                           uint2 seed, int lane, int32_t* rec_count,
+                                           const uint2* pre, uint2* pbuf) {
+  constexpr int B = long_visit_b<CPL>();
   constexpr int NS = B + B * (B - 1) / 2;
   static_assert(NS <= 32, "one transposed reduction per block");
-  // blocks of rows in flight; positions up to B*(b + LB) + B - 1 must lie in
-  // record chunks c0 and c0 + 1
-  constexpr int LB = (NCH / CPL) / B < 33 / B - 1 ? (NCH / CPL) / B : 33 / B - 1;
+  constexpr int LB = long_visit_lb<CPL, NCH>();
   static_assert(LB >= 1 && B * (LB + 1) - 1 <= 32, "row ring holds the blocks in flight");
   using w_t = typename Fmt<PR>::w_t;
   const float al = 1.f - s * lam;
@@ -439,6 +456,17 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Fmt<PR>::w
         }
         if constexpr (PR == kFP8)
           if (lane == 0) cp_async4(rsc + set * B + i, Wscale + row);
+        if constexpr (PR != kF32) {
+          if constexpr (PRE) {
+            const int pset = int(unsigned(bb) % unsigned(LB + 1));
+#pragma unroll
+            for (int cc = 0; cc < CPL; ++cc) {
+              const int idx = lane + 32 * cc;
+              if (idx < k4)
+                cp_async8(pbuf + ((pset * B + i) * CPL + cc) * 32 + lane, pre + int64_t(u) * k4 + idx);
+            }
+          }
+        }
       }
     }
     cp_commit();
@@ -498,9 +526,13 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Fmt<PR>::w
     // the block's rounding bits (narrow formats): independent of the
     // updates, drawn here so that the draws overlap the reduction below
     if constexpr (PR != kF32) {
-      __syncwarp();  // every lane has read the previous block's bits
-      draw_w_bits<CPL>(rbuf, B, beg + b * B + (lane < B ? lane : 0), epoch, k4, seed, lane);
+      if constexpr (!PRE) {
+        __syncwarp();  // every lane has read the previous block's bits
+        draw_w_bits<CPL>(rbuf, B, beg + b * B + (lane < B ? lane : 0), epoch, k4, seed, lane);
+      }
     }
+    // the block's rounding bits
+    const uint2* bits = PRE ? pbuf + int(unsigned(b) % unsigned(LB + 1)) * B * CPL * 32 : rbuf;
     const float red = warp_sum_transposed(v, lane);
     // lane u < B: A_u - a^u <w_u, h_0>, then the forward substitution
     float acc;
@@ -562,7 +594,7 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Fmt<PR>::w
         e4m3_row_scale(am[i], &sc, &g);
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc) {
-          const uint2 rb = rbuf[i * CPL * 32 + lane + 32 * cc];
+          const uint2 rb = bits[i * CPL * 32 + lane + 32 * cc];
           if (lane + 32 * cc < k4) wrow[lane + 32 * cc] = e4m3_pack(wn[i][cc], g, true, rb.x, rb.y);
         }
         if (lane == 0) Wscale[row] = sc;
@@ -587,7 +619,7 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Fmt<PR>::w
       uint2 rb[CPL];
       if constexpr (PR != kF32) {
 #pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) rb[cc] = rbuf[i * CPL * 32 + lane + 32 * cc];
+        for (int cc = 0; cc < CPL; ++cc) rb[cc] = bits[i * CPL * 32 + lane + 32 * cc];
       }
       w_t out[CPL];
       float scale = 1.f;
@@ -647,9 +679,14 @@ __device__ __forceinline__ bool inbox_push(unsigned char* ib, int j, int4 a, int
 // interrupted work), h_j back to H, the token handed on at once.  Visits are
 // never split: the check runs between visits.  Not inlined: it is reached
 // from two places and runs a few hundred times per worker and epoch.
-template <int PR, bool DEBUG, bool BLK>
+// An urgent visit with pre-drawn bits keeps LB + 1 blocks of them in the
+// stream's rounding-bits area (the stream draws its bits again afterwards).
+static_assert((long_visit_lb<1, kUrgentChunks>() + 1) * long_visit_b<1>() <= 32,
+              "the stream's bits area holds an urgent visit's blocks of bits");
+template <int PR, bool DEBUG, bool BLK, bool PRE>
 __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, uint32_t item,
-                                          typename Fmt<PR>::w_t* rows, float* rsc, uint2* rbuf) {
+                                          typename Fmt<PR>::w_t* rows, float* rsc, uint2* rbuf,
+                                          uint2* pbuf) {
   using w_t = typename Fmt<PR>::w_t;
   using h_t = typename Fmt<PR>::h_t;
   w_t* __restrict__ W4 = reinterpret_cast<w_t*>(P.W);
@@ -687,8 +724,11 @@ __device__ __noinline__ void urgent_visit(const SgdParams& P, int q, int lane, u
     }
     if (atomicExch(P.owner + uj, q) != -1) flag_ownership(P, q, uj);
   }
-  long_visit<1, PR, DEBUG, kUrgentChunks>(uh, rows, rsc, rbuf, W4, P.Wscale, pitch4, k4, P.rec,
-                                          ubeg, uc, us, P.lambda, ue, seed, lane, P.rec_count);
+  // PRE: the rounding bits were drawn before the launch (narrow formats)
+  const uint2* pre = PRE ? P.ubits_pre + P.useg_off[useg] * k4 : nullptr;
+  long_visit<1, PR, DEBUG, kUrgentChunks, PRE>(uh, rows, rsc, rbuf, W4, P.Wscale, pitch4, k4,
+                                               P.rec, ubeg, uc, us, P.lambda, ue, seed, lane,
+                                               P.rec_count, pre, pbuf);
   if (lane < k4) store_h(H4 + int64_t(uj) * pitch4 + lane, uh[0], int(useg), ue, lane, seed);
   if (lane == 0) {
     if (unseg >= 0) {
@@ -786,8 +826,12 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       useg = __shfl_sync(kFull, useg, 0);
       ++head_u;
       ++done;
-      urgent_visit<PR, DEBUG, BLK>(P, q, lane, useg, rows + kVisitChunks * 32, rsc + kVisitChunks,
-                                   ubits);
+      if (PR != kF32 && P.ubits_pre)
+        urgent_visit<PR, DEBUG, BLK, PR != kF32>(P, q, lane, useg, rows + kVisitChunks * 32,
+                                                 rsc + kVisitChunks, ubits, srb);
+      else
+        urgent_visit<PR, DEBUG, BLK, false>(P, q, lane, useg, rows + kVisitChunks * 32,
+                                            rsc + kVisitChunks, ubits, srb);
       return true;
     }
   };
@@ -822,8 +866,12 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       const uint32_t item = uint32_t(__shfl_sync(kFull, sv, 31));
       ++head_u;
       ++done;
-      urgent_visit<PR, DEBUG, BLK>(P, q, lane, item, rows + kVisitChunks * 32, rsc + kVisitChunks,
-                                   ubits);
+      if (PR != kF32 && P.ubits_pre)
+        urgent_visit<PR, DEBUG, BLK, PR != kF32>(P, q, lane, item, rows + kVisitChunks * 32,
+                                                 rsc + kVisitChunks, ubits, srb);
+      else
+        urgent_visit<PR, DEBUG, BLK, false>(P, q, lane, item, rows + kVisitChunks * 32,
+                                            rsc + kVisitChunks, ubits, srb);
       continue;
     }
     // inbox tokens: the ready positions from the head on, in order
@@ -1015,7 +1063,7 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       }
       long_visit<CPL, PR, DEBUG, RowRing<CPL>::VISIT>(hh, rows, rsc, srb, W4, Wscale, pitch4, k4,
                                                       P.rec, vb, ma.y, sv, lam, ma.z, seed, lane,
-                                                      P.rec_count);
+                                                      P.rec_count, nullptr, nullptr);
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int idx = lane + 32 * cc;
@@ -1091,6 +1139,10 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
             copy_row(pos % R, recs[pos % kRecBuf].x);
           cp_commit();
           cp_wait<0>();
+          // a visit with pre-drawn bits used the stream's bits area: draw
+          // from t again
+          if constexpr (PR != kF32)
+            if (P.ubits_pre) sr_hi = t;
         }
         ++k;
         const int4 ma = meta_a[k];

@@ -345,6 +345,29 @@ __global__ void urgent_flags(const uint32_t* __restrict__ deg, int64_t n,
     flag[j] = deg[j] > 0 && 2ull * deg[j] >= top ? 1 : 0;
 }
 
+// Segment s of an urgent item: its number of ratings in len[s] and 1 in
+// flag[s] (0, 0 for the other segments).
+__global__ void urgent_seg_lengths(const int64_t* __restrict__ seg_ptr,
+                                   const int32_t* __restrict__ seg_col,
+                                   const uint8_t* __restrict__ item_urgent, int64_t S,
+                                   int64_t* __restrict__ len, uint32_t* __restrict__ flag) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < S; s += stride) {
+    const bool u = item_urgent[seg_col[s]] != 0;
+    len[s] = u ? seg_ptr[s + 1] - seg_ptr[s] : 0;
+    flag[s] = u ? 1u : 0u;
+  }
+}
+
+// The urgent segments in order: list[pos[s]] = s where flag[s].
+__global__ void urgent_seg_scatter(const uint32_t* __restrict__ flag,
+                                   const uint32_t* __restrict__ pos, int64_t S,
+                                   int32_t* __restrict__ list) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < S; s += stride)
+    if (flag[s]) list[pos[s]] = int32_t(s);
+}
+
 __global__ void count_flags(const uint8_t* __restrict__ flag, int64_t n,
                             uint32_t* __restrict__ count) {
   uint32_t c = 0;
@@ -679,6 +702,53 @@ int build_layout(nomad_handle* h, int64_t nnz, const int32_t* d_rows,
     TRY(dev_alloc(h, &vp, sizeof(unsigned long long) * (int64_t(p) << lgu)));
     h->uring = (unsigned long long*)vp;
     TRY(dev_alloc(h, &vp, sizeof(uint32_t) * (p + 1))); h->uring_tail = (uint32_t*)vp;
+
+    // 10b. narrow formats: room for the W rounding bits of the urgent items'
+    // ratings, drawn before each launch so that the chains of visits of
+    // these items do not wait for them (the batched kernel at one chunk
+    // per lane, epoch mode).  It pays where a few items with very long
+    // chains bind the epoch: only when their ratings are at most a quarter
+    // of all (with more, as for degrees close to uniform, the pass costs
+    // more than the chains gain), and at most a quarter of the free device
+    // memory or 32 GiB
+    if (h->sched.precision != NOMAD_FP32 && h->sched.variant == NOMAD_VARIANT_BATCHED &&
+        h->sched.mode == NOMAD_MODE_EPOCH && h->k4 <= 32 && S > 0 && n_urgent > 0) {
+      int64_t* len = nullptr;
+      uint32_t *flag3 = nullptr, *pos = nullptr;
+      TRY(cudaMallocAsync(&len, sizeof(int64_t) * salloc, st));
+      TRY(cudaMallocAsync(&flag3, sizeof(uint32_t) * salloc, st));
+      TRY(cudaMallocAsync(&pos, sizeof(uint32_t) * (S + 1), st));
+      TRY(dev_alloc(h, &vp, sizeof(int64_t) * (S + 1))); h->useg_off = (int64_t*)vp;
+      urgent_seg_lengths<<<grid_for(S), 256, 0, st>>>(h->seg_ptr, h->seg_col, h->item_urgent, S,
+                                                      len, flag3);
+      ++t_launches;
+      TRY((exclusive_scan<int64_t, int64_t>(len, h->useg_off, S, h->useg_off + S, st)));
+      TRY((exclusive_scan<uint32_t, uint32_t>(flag3, pos, S, pos + S, st)));
+      int64_t urecs = 0;
+      uint32_t nus = 0;
+      TRY(cudaMemcpyAsync(&urecs, h->useg_off + S, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      TRY(cudaMemcpyAsync(&nus, pos + S, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      TRY(cudaStreamSynchronize(st));
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      const double bytes = double(urecs) * double(h->k4) * sizeof(uint2);
+      if (nus > 0 && urecs * 4 <= nnz && bytes <= double(free_b) / 4 &&
+          bytes <= double(int64_t(32) << 30)) {
+        TRY(dev_alloc(h, &vp, sizeof(int32_t) * nus)); h->useg_list = (int32_t*)vp;
+        urgent_seg_scatter<<<grid_for(S), 256, 0, st>>>(flag3, pos, S, h->useg_list);
+        ++t_launches;
+        TRY(dev_alloc(h, &vp, size_t(bytes))); h->ubits_pre = (uint2*)vp;
+        h->n_useg = int64_t(nus);
+        h->upre_records = urecs;
+      } else {
+        vp = h->useg_off;
+        dev_free(h, &vp);
+        h->useg_off = nullptr;
+      }
+      cudaFreeAsync(len, st);
+      cudaFreeAsync(flag3, st);
+      cudaFreeAsync(pos, st);
+    }
   }
   if (h->sched.debug || h->sched.mode == NOMAD_MODE_UNIFORM) {
     TRY(dev_alloc(h, &vp, sizeof(int32_t) * nalloc)); h->rec_count = (int32_t*)vp;

@@ -55,8 +55,11 @@ void free_layout(nomad_handle* h) {
                    (void**)&h->rec_count,  (void**)&h->log_seg,   (void**)&h->log_epoch,
                    (void**)&h->item_urgent, (void**)&h->uring,    (void**)&h->uring_tail,
                    (void**)&h->tok_rec,    (void**)&h->ring_head,  (void**)&h->col_grp_ptr,
-                   (void**)&h->grp_off};
+                   (void**)&h->grp_off,    (void**)&h->useg_off,  (void**)&h->useg_list,
+                   (void**)&h->ubits_pre};
   for (void** p : ptrs) dev_free(h, p);
+  h->n_useg = 0;
+  h->upre_records = 0;
   h->log_cap = 0;
   h->loaded = false;
   h->nnz = 0;
@@ -591,6 +594,7 @@ int nomad_get_info(const nomad_t* h, nomad_info* out) {
   out->sm_count = h->sm_count;
   out->device_bytes = h->device_bytes;
   out->kernel_launches = h->launches;
+  out->predrawn_ratings = h->ubits_pre ? h->upre_records : 0;
   return NOMAD_OK;
 }
 

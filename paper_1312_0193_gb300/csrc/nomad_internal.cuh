@@ -248,6 +248,12 @@ struct SgdParams {
   int32_t* owner;
   int32_t* rec_count;
   int32_t drop_item;
+  // narrow formats, one epoch per launch: the W rounding bits of the urgent
+  // items' ratings for this epoch, drawn before the launch (a record's bits
+  // at ubits_pre[(useg_off[s] + r - seg_ptr[s]) * k4 + chunk] for record r
+  // of urgent segment s), or null (the kernel draws them)
+  const int64_t* useg_off;
+  const uint2* ubits_pre;
 };
 
 
@@ -304,6 +310,13 @@ struct nomad_handle {
   int32_t* tok_hop = nullptr;
   int32_t* tok_epoch = nullptr;
   uint8_t* item_urgent = nullptr;  // n: item degree >= half the largest
+  // narrow formats: W rounding bits of the urgent items' ratings, drawn
+  // before each launch (section 10b of the layout build); null if not used
+  int64_t* useg_off = nullptr;     // S: offset (records) of an urgent segment's bits
+  int32_t* useg_list = nullptr;    // the urgent segments
+  int64_t n_useg = 0;
+  int64_t upre_records = 0;        // records of the urgent segments
+  uint2* ubits_pre = nullptr;      // urgent records x k4
   int4* tok_rec = nullptr;         // 4n: next-visit record of each token
   float* step = nullptr;
   int32_t step_cap = 0;
@@ -353,6 +366,11 @@ const void* batched_kernel(int k4, bool debug, int precision, bool many, bool bl
                            size_t* smem_per_warp);
 size_t batched_inbox_bytes();   // per warp, hybrid circulation only
 size_t batched_params_bytes();  // per block, several-problem form
+// Draws the W rounding bits of epoch `epoch` for every record of the urgent
+// segments useg_list[0 .. n_useg) into out (layout of SgdParams::ubits_pre).
+cudaError_t draw_urgent_bits(const int32_t* useg_list, int64_t n_useg, const int64_t* seg_ptr,
+                             const int64_t* useg_off, int k4, int epoch, uint2 seed, uint2* out,
+                             cudaStream_t st);
 
 // Initialisation, evaluation and factor copies (eval.cu).
 int init_factors(nomad_handle* h, cudaStream_t stream);

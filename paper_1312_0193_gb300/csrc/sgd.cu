@@ -468,6 +468,11 @@ int prepare_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st, SgdParams
   P.step = h->step;
   P.epoch0 = int32_t(h->epochs_done) + epoch_off;
   P.n_epochs = n_epochs;
+  // the urgent items' rounding bits are drawn before a launch of one epoch
+  if (h->ubits_pre && n_epochs == 1 && P.use_urgent) {
+    P.useg_off = h->useg_off;
+    P.ubits_pre = h->ubits_pre;
+  }
   P.p = h->p;
   P.lambda = h->lambda;
   P.alpha = h->sched.alpha;
@@ -561,8 +566,15 @@ int launch_epochs(nomad_handle* h, int32_t n_epochs, cudaStream_t st) {
     }
     void* args[] = {&P};
     if (done == 0) cudaEventRecord(h->ev_start, st);
-    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(h->blocks),
-                                                      dim3(h->warps_per_block * 32), args, smem, st);
+    cudaError_t e = cudaSuccess;
+    if (P.ubits_pre) {
+      e = draw_urgent_bits(h->useg_list, h->n_useg, h->seg_ptr, h->useg_off, h->k4, P.epoch0,
+                           make_uint2(P.seed_lo, P.seed_hi), h->ubits_pre, st);
+      ++h->launches;
+    }
+    if (e == cudaSuccess)
+      e = cudaLaunchCooperativeKernel(fn, dim3(h->blocks), dim3(h->warps_per_block * 32), args,
+                                      smem, st);
     if (e != cudaSuccess) {
       h->last_error = std::string("epoch: cooperative launch: ") + cudaGetErrorString(e);
       return NOMAD_ERR_CUDA;
@@ -617,6 +629,7 @@ int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cud
     const int32_t ne = n_epochs - done < per ? n_epochs - done : per;
     std::vector<SgdParams> Ps;
     std::vector<int2> blocks;
+    std::vector<int> pre;  // handles whose urgent rounding bits are drawn first
     Ps.reserve(size_t(count));
     for (int g = 0; g < count; ++g) {
       SgdParams P{};
@@ -626,6 +639,7 @@ int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cud
         return rc;
       }
       if (hs[g]->nnz == 0) continue;
+      if (P.ubits_pre) pre.push_back(g);
       for (int b = 0; b < hs[g]->blocks; ++b) blocks.push_back(make_int2(int(Ps.size()), b));
       Ps.push_back(P);
     }
@@ -639,10 +653,20 @@ int launch_epochs_many(nomad_handle* const* hs, int count, int32_t n_epochs, cud
     if (!e) {
       if (done == 0)
         for (int g = 0; g < count; ++g) cudaEventRecord(hs[g]->ev_start, st);
+      for (size_t i = 0; i < pre.size() && !e; ++i) {
+        nomad_handle* hg = hs[pre[i]];
+        e = draw_urgent_bits(hg->useg_list, hg->n_useg, hg->seg_ptr, hg->useg_off, hg->k4,
+                             int32_t(hg->epochs_done) + done,
+                             make_uint2(uint32_t(hg->sched.seed), uint32_t(hg->sched.seed >> 32)),
+                             hg->ubits_pre, st);
+        ++hg->launches;
+      }
       const SgdParams* aP = static_cast<const SgdParams*>(dP);
       const int2* aB = static_cast<const int2*>(dB);
       void* args[] = {&aP, &aB, &use_inboxes};
-      e = cudaLaunchCooperativeKernel(fn, dim3(unsigned(blocks.size())), dim3(wpb * 32), args, smem, st);
+      if (!e)
+        e = cudaLaunchCooperativeKernel(fn, dim3(unsigned(blocks.size())), dim3(wpb * 32), args,
+                                        smem, st);
       if (!e) ++h0->launches;
     }
     if (dP) cudaFreeAsync(dP, st);

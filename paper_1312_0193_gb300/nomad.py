@@ -65,7 +65,7 @@ class nomad_info(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks", ctypes.c_int32), ("sm_count", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("predrawn_ratings", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
 
 # name -> (restype, argtypes); mirrors include/nomad.h
