@@ -455,14 +455,18 @@ def run_sweep(args):
              for b in sweep_blocks(nnz, sms)]
     tuning = []
 
+    best = None  # (launch ms, knobs) of the fastest trial so far
+
     def trial(kn, what):
+        nonlocal best
         ms, spans = calibrate(kn)
         tuning.append({"trial": what, "kernel_ms": round(ms, 2),
                        "slowest_span_ms": round(max(spans) / 1e6, 2),
                        "mean_span_ms": round(statistics.mean(spans) / 1e6, 2)})
+        if best is None or ms < best[0]:
+            best = (ms, [dict(k) for k in kn])
         return ms, spans
 
-    best = None
     if args.sweep_tune > 0:
         ms_flat, sp_flat = trial(knobs, "flat circulation, 16 tokens")
         alt = [dict(k, circulation="block") for k in knobs]
@@ -475,7 +479,6 @@ def run_sweep(args):
         knobs = [dict(k, batch_tokens=8 if e < s_ else 0)
                  for k, s_, e in zip(knobs, sp16, sp8)]
         ms, spans = trial(knobs, "per-problem circulation and tokens")
-        best = (ms, [dict(k) for k in knobs])
         for _ in range(args.sweep_tune):
             blocks = sweep_blocks([max(sp, 1) * k["blocks"] for sp, k in zip(spans, knobs)],
                                   sms)
@@ -483,9 +486,7 @@ def run_sweep(args):
                 break
             knobs = [dict(k, blocks=b) for k, b in zip(knobs, blocks)]
             ms, spans = trial(knobs, "blocks re-allocated")
-            if ms < best[0]:
-                best = (ms, [dict(k) for k in knobs])
-        knobs = best[1]
+        knobs = best[1]  # the fastest of all trials
     many = handles(knobs)
     alone = handles([{"blocks": 0, "circulation": "flat", "batch_tokens": 0}] * len(specs))
     stream = torch.cuda.current_stream(dev)
