@@ -264,6 +264,45 @@ def test_set_get_factors_roundtrip(tiny):
     assert np.array_equal(W, W2) and np.array_equal(H, H2)
 
 
+def test_resume_from_checkpoint_replays(tiny):
+    """Checkpoint and resume: a handle runs 2 epochs, its factors go to the
+    host, a new handle takes them with epochs_done = 2 and runs 2 more in
+    debug mode.  Its log has epochs 2 and 3 only, and the oracle's replay of
+    it from the checkpoint (every rating's update count starting at 2, so
+    the step sizes continue at t = 2) matches within the replay bound."""
+    lam, alpha, beta = 0.05, 0.02, 0.05
+    with make(tiny, 10, lam, alpha=alpha, beta=beta, n_workers=16) as nm:
+        nm.epoch(2)
+        nm.check()
+        W1, H1 = nm.factors()
+    a32, b32, lam32 = (float(np.float32(x)) for x in (alpha, beta, lam))
+    with make(tiny, 10, lam, alpha=alpha, beta=beta, n_workers=16, debug=True) as nm:
+        nm.set_factors(W1, H1, epochs_done=2)
+        assert nm.info()["epochs_done"] == 2
+        L, _ = oracle_layout(nm, tiny)
+        nm.epoch(2)
+        nm.check()
+        seg, ep = nm.replay_log()
+        Wg, Hg = nm.factors()
+        counts, viol = nm.debug_counts()
+        assert nm.info()["epochs_done"] == 4
+    assert viol == 0 and np.all(counts == 2)
+    assert ep.min() == 2 and ep.max() == 3
+    S = L["seg_col"].size
+    for e in (2, 3):
+        assert np.array_equal(np.sort(seg[ep == e]), np.arange(S))
+    start = np.full(L["rec_row"].size, 2, np.int32)
+    Wo, Ho, cnt = oracle.replay(L, seg, W1, H1, lam32, a32, b32, precision="f32",
+                                rec_count=start)
+    assert np.all(cnt == 4)
+    for g, o in ((Wg, Wo), (Hg, Ho)):
+        assert rel(g, o) < REPLAY_TOL, rel(g, o)
+        assert row_rel_max(g, o) < ROW_TOL, row_rel_max(g, o)
+    # the step sizes matter: replayed as if from epoch 0 the result differs
+    Wz, _, _ = oracle.replay(L, seg, W1, H1, lam32, a32, b32, precision="f32")
+    assert rel(Wz, Wo) > 10 * REPLAY_TOL
+
+
 # ---------------------------------------------------------------- failure path
 def test_lost_token_times_out_and_recovers(tiny):
     """A planted lost message (one item's token never handed out): the worker
