@@ -57,12 +57,15 @@ def test_bf16_only_with_batched_epoch_kernel():
         Nomad(10, 10, 4, 0.1, precision="bf16", mode="uniform")
 
 
-@pytest.mark.parametrize("k,p,epochs,alpha", [(10, 64, 10, 0.05), (100, 40, 2, 0.01)])
-def test_bf16_replay(k, p, epochs, alpha):
+@pytest.mark.parametrize("k,p,epochs,alpha,circ", [(10, 64, 10, 0.05, "flat"),
+                                                   (100, 40, 2, 0.01, "flat"),
+                                                   (100, 64, 2, 0.01, "block")])
+def test_bf16_replay(k, p, epochs, alpha, circ):
     r = synth.tiny_planted(1) if k == 10 else synth.netflix_shaped(0.0005, seed=3)
     tr, tc, tv, *_ = r.numpy()
     lam, beta, seed = 0.05, 0.05, 11
-    with make(r, k, lam, alpha=alpha, beta=beta, debug=True, n_workers=p, seed=seed) as nm:
+    with make(r, k, lam, alpha=alpha, beta=beta, debug=True, n_workers=p, seed=seed,
+              circulation=circ) as nm:
         rw = oracle.partition_rows(r.m, tr, p)
         L = oracle.build_layout(r.m, r.n, tr, tc, tv, rw, p)
         W0, H0 = nm.factors()

@@ -86,12 +86,12 @@ def test_fp8_only_with_batched_epoch_kernel():
         Nomad(10, 10, 4, 0.1, precision="fp8", mode="uniform")
 
 
-def fp8_replay(r, k, p, epochs, alpha, lam=0.05, beta=0.05, seed=11):
+def fp8_replay(r, k, p, epochs, alpha, lam=0.05, beta=0.05, seed=11, **kw):
     """A debug run on the GPU and the oracle's E4M3 replay of its logged
     order from the oracle's own initial factors: (GPU W, H, oracle W, H)."""
     tr, tc, tv, *_ = r.numpy()
     with Nomad(r.m, r.n, k, lam, alpha=alpha, beta=beta, debug=True, n_workers=p, seed=seed,
-               precision="fp8") as nm:
+               precision="fp8", **kw) as nm:
         nm.load_coo(r.train_rows.cuda(), r.train_cols.cuda(), r.train_vals.cuda())
         rw = oracle.partition_rows(r.m, tr, p)
         L = oracle.build_layout(r.m, r.n, tr, tc, tv, rw, p)
@@ -112,15 +112,17 @@ def fp8_replay(r, k, p, epochs, alpha, lam=0.05, beta=0.05, seed=11):
     return Wg, Hg, oracle.e4m3_decode_rows(Wc, Ws), Ho
 
 
-@pytest.mark.parametrize("k,p", [(10, 64), (100, 40), (100, 4)])
-def test_fp8_replay_zero_step_bit_exact(k, p):
+@pytest.mark.parametrize("k,p,circ", [(10, 64, "flat"), (100, 40, "flat"), (100, 4, "flat"),
+                                      (100, 64, "block")])
+def test_fp8_replay_zero_step_bit_exact(k, p, circ):
     """With a zero step both sides hold bit-identical binary32 values at
     every write (w' = w, h' = h), so every stochastic rounding decision,
     every re-derived scale and every forwarded row must agree exactly: the
     GPU's stored W equals the oracle's replay bit for bit.  p = 4 gives long
-    visits (the block form) and rows forwarded between positions in flight."""
+    visits (the block form) and rows forwarded between positions in flight;
+    the hybrid circulation hands tokens over through shared-memory inboxes."""
     r = synth.tiny_planted(1) if k == 10 else synth.netflix_shaped(0.0005, seed=3)
-    Wg, Hg, Wo, Ho = fp8_replay(r, k, p, 2, 0.0)
+    Wg, Hg, Wo, Ho = fp8_replay(r, k, p, 2, 0.0, circulation=circ)
     assert np.array_equal(Wg, Wo)
     assert np.array_equal(Hg, Ho)
 
