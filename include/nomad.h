@@ -212,8 +212,9 @@ NOMAD_API int nomad_load_ratings(nomad_t *h, int32_t fmt, int64_t nnz, const voi
  * nomad_get_factors call. */
 NOMAD_API int nomad_epoch(nomad_t *h, int32_t n_epochs, void *stream);
 
-/* nomad_epoch for `count` independent problems at once: one persistent
- * launch in which each problem runs on its own blocks (h[g]->n_workers
+/* nomad_epoch for `count` independent problems at once: per epoch one
+ * persistent launch (or per the first handle's epochs_per_launch) in which
+ * each problem runs on its own blocks (h[g]->n_workers
  * workers, i.e. its schedule's n_workers / warps_per_block blocks), as in a
  * sweep over lambda, k or data (App. A/B).  The problems share no data; each
  * one's updates, visit order, replay log and errors are those nomad_epoch
@@ -226,7 +227,8 @@ NOMAD_API int nomad_epoch(nomad_t *h, int32_t n_epochs, void *stream);
  *    warps_per_block warps per SM with the default shared memory use):
  *    otherwise NOMAD_ERR_UNSUPPORTED and nothing runs.
  *  - Asynchronous on `stream`; per-handle errors as for nomad_epoch, and
- *    nomad_last_epoch_kernel_ms of every handle reports the one launch.
+ *    nomad_last_epoch_kernel_ms of every handle reports the call's
+ *    launches (first start to last end).
  * Errors: NOMAD_ERR_INVALID_ARG (count < 1, a NULL or repeated handle,
  * n_epochs < 1), NOMAD_ERR_STATE (a handle without ratings),
  * NOMAD_ERR_UNSUPPORTED (handles that differ in the above, or too many

@@ -299,8 +299,8 @@ class Nomad:
 
     @staticmethod
     def epoch_many(nomads, n_epochs=1, stream=None):
-        """n_epochs epochs of several independent problems in one launch
-        (nomad_epoch_many): each handle runs on its own blocks."""
+        """n_epochs epochs of several independent problems, one launch per
+        epoch (nomad_epoch_many): each handle runs on its own blocks."""
         nomad_epoch_many([nm.h for nm in nomads], n_epochs, _stream_ptr(stream))
 
     def check(self, stream=None):

@@ -53,8 +53,9 @@ PROBLEMS = [
 
 
 def test_many_replay_each_problem():
-    """Three problems, two calls of 3 epochs each in one launch per call;
-    every problem replays on the oracle as if it had run alone."""
+    """Three problems, two calls of 3 epochs each (one launch per epoch, all
+    problems in it); every problem replays on the oracle as if it had run
+    alone."""
     epochs, calls = 3, 2
     runs = []
     try:
@@ -100,8 +101,9 @@ def test_many_replay_each_problem():
 
 
 def test_many_free_run_matches_alone():
-    """Four problems, 10 epochs in one launch: each problem's test RMSE is
-    within 0.5% of the same problem run alone with the same workers."""
+    """Four problems, 10 epochs together (one launch per epoch): each
+    problem's test RMSE is within 0.5% of the same problem run alone with
+    the same workers."""
     specs = [(synth.tiny_planted(1), 10, 0.05, 16),
              (synth.netflix_shaped(0.002, seed=13), 100, 0.05, 40),
              (synth.netflix_shaped(0.001, seed=21), 32, 0.05, 24),
@@ -116,14 +118,15 @@ def test_many_free_run_matches_alone():
         Nomad.epoch_many(nms, 10)
         ms = nms[0].last_epoch_kernel_ms()
         spans = [nm.last_epoch_span_ns() for nm in nms]
-        # each problem's device span lies within the launch (CUDA events),
-        # and the launch lasts about as long as its slowest problem
+        # each problem's device span lies within the call (CUDA events
+        # around its launches), and the call lasts about as long as its
+        # slowest problem
         assert all(0 < s <= ms * 1e6 * 1.02 + 5e4 for s in spans), (spans, ms)
         assert max(spans) >= 0.5 * ms * 1e6, (spans, ms)
         for nm, (r, *_rest) in zip(nms, specs):
             nm.check()
             together.append(nm.rmse(*r.numpy()[3:]))
-            # every handle records its own events around the one launch
+            # every handle records its own events around the call's launches
             assert abs(nm.last_epoch_kernel_ms() - ms) < 0.05
     finally:
         for nm in nms:
