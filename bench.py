@@ -627,13 +627,15 @@ def time_to_target(args, dev, local):
                    seed=int(t.get("init_seed", 1)))
         nm.load_coo(r.train_rows, r.train_cols, r.train_vals)
         secs, ep, rm = 0.0, 0, float("inf")
+        trace = []  # test RMSE against GPU seconds (Sec. 5.1's curves)
         while ep < 2 * E and not rm <= target:
             nm.epoch(1)
             secs += nm.last_epoch_kernel_ms() / 1e3
             rm = nm.rmse(r.test_rows, r.test_cols, r.test_vals)
             ep += 1
+            trace.append([ep, round(secs, 5), round(rm, 6)])
         out[prec] = {"reached": bool(rm <= target), "epochs": ep, "seconds": secs,
-                     "test_rmse": rm}
+                     "test_rmse": rm, "trace_epoch_seconds_rmse": trace}
         nm.close()
     return out
 
