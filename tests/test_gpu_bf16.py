@@ -59,7 +59,9 @@ def test_bf16_only_with_batched_epoch_kernel():
 
 @pytest.mark.parametrize("k,p,epochs,alpha,circ", [(10, 64, 10, 0.05, "flat"),
                                                    (100, 40, 2, 0.01, "flat"),
-                                                   (100, 64, 2, 0.01, "block")])
+                                                   (100, 64, 2, 0.01, "block"),
+                                                   (130, 16, 2, 0.01, "flat"),
+                                                   (300, 8, 2, 0.01, "flat")])
 def test_bf16_replay(k, p, epochs, alpha, circ):
     r = synth.tiny_planted(1) if k == 10 else synth.netflix_shaped(0.0005, seed=3)
     tr, tc, tv, *_ = r.numpy()

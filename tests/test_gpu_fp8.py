@@ -113,7 +113,7 @@ def fp8_replay(r, k, p, epochs, alpha, lam=0.05, beta=0.05, seed=11, **kw):
 
 
 @pytest.mark.parametrize("k,p,circ", [(10, 64, "flat"), (100, 40, "flat"), (100, 4, "flat"),
-                                      (100, 64, "block")])
+                                      (100, 64, "block"), (130, 16, "flat"), (300, 8, "flat")])
 def test_fp8_replay_zero_step_bit_exact(k, p, circ):
     """With a zero step both sides hold bit-identical binary32 values at
     every write (w' = w, h' = h), so every stochastic rounding decision,
@@ -122,6 +122,7 @@ def test_fp8_replay_zero_step_bit_exact(k, p, circ):
     visits (the block form) and rows forwarded between positions in flight;
     the hybrid circulation hands tokens over through shared-memory inboxes."""
     r = synth.tiny_planted(1) if k == 10 else synth.netflix_shaped(0.0005, seed=3)
+    # k = 130 and 300: two and four chunks of a row per lane
     Wg, Hg, Wo, Ho = fp8_replay(r, k, p, 2, 0.0, circulation=circ)
     assert np.array_equal(Wg, Wo)
     assert np.array_equal(Hg, Ho)

@@ -161,3 +161,48 @@ def test_many_rejects_what_it_cannot_run():
     finally:
         for x in [a, b, c, d] + big:
             x.close()
+
+
+def test_many_bf16_replay_with_predrawn_bits():
+    """bfloat16 storage, two problems together for one epoch: one whose
+    most-rated item holds a small share of the ratings (its rounding bits
+    are drawn before the launch) and the tiny planted one (drawn in the
+    kernel); each replays on the oracle's bfloat16 replay within 1e-2
+    relative L2 (the bound of the one-problem bfloat16 test)."""
+    rng = np.random.default_rng(3)
+    m, n = 3000, 400
+    mask = rng.random((m - 1000, n - 1)) < 0.05
+    rr, cc = np.nonzero(mask)
+    rows = np.concatenate([np.arange(m), rr + 1000]).astype(np.int32)
+    cols = np.concatenate([np.zeros(m, np.int64), cc + 1]).astype(np.int32)
+    vals = rng.normal(3.5, 1.0, size=rows.size).astype(np.float32)
+    heavy = synth.Ratings(m, n, torch.from_numpy(rows), torch.from_numpy(cols),
+                          torch.from_numpy(vals), torch.zeros(0, dtype=torch.int32),
+                          torch.zeros(0, dtype=torch.int32), torch.zeros(0))
+    seed, lam, alpha, beta = 11, 0.05, 0.01, 0.05
+    runs = []
+    try:
+        for r, k, p in ((heavy, 32, 16), (synth.tiny_planted(1), 10, 16)):
+            nm = make(r, k, lam, alpha=alpha, beta=beta, debug=True, n_workers=p, seed=seed,
+                      precision="bf16")
+            tr, tc, tv, *_ = r.numpy()
+            L = oracle.build_layout(r.m, r.n, tr, tc, tv, oracle.partition_rows(r.m, tr, p), p)
+            runs.append((nm, L, nm.factors()))
+        assert runs[0][0].info()["predrawn_ratings"] == m
+        assert runs[1][0].info()["predrawn_ratings"] == 0
+        Nomad.epoch_many([x[0] for x in runs], 1)
+        f32 = lambda x: float(np.float32(x))
+        for nm, L, (W0, H0) in runs:
+            nm.check()
+            seg, ep = nm.replay_log()
+            Wg, Hg = nm.factors()
+            counts, viol = nm.debug_counts()
+            assert viol == 0 and np.all(counts == 1)
+            Wb, Hb, cnt = oracle.replay_bf16(L, seg, ep, oracle.bf16_rn(W0), oracle.bf16_rn(H0),
+                                             f32(lam), f32(alpha), f32(beta), seed)
+            assert np.array_equal(cnt, counts)
+            assert rel(Wg, oracle.bf16_to_f32(Wb)) < 1e-2
+            assert rel(Hg, oracle.bf16_to_f32(Hb)) < 1e-2
+    finally:
+        for x in runs:
+            x[0].close()
