@@ -300,18 +300,20 @@ __device__ __forceinline__ void cp_wait() {
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// The visit rank of stream position p: the last rank r < nb whose offset is
-// <= p.  Lane r < nb holds the stream offset `soff` of the rank-r visit
-// (offsets increase with the rank).
+// The visit rank of stream position p (p0 <= p < p0 + 32): the last rank
+// r < nb whose offset is <= p.  Lane r < nb holds the stream offset `soff`
+// of the rank-r visit (offsets increase strictly with the rank): the visits
+// that start before p0 are counted with one ballot, those that start in
+// [p0, p] with one OR-reduction of their start bits.
 template <int KB>
-__device__ __forceinline__ int rank_of(int soff, int nb, int p) {
-  int r = 0;
-#pragma unroll
-  for (int i = 1; i < KB; ++i) {
-    const int o = __shfl_sync(kFull, soff, i);
-    if (i < nb && o <= p) r = i;
-  }
-  return r;
+__device__ __forceinline__ int rank_of(int soff, int nb, int p0, int p, int lane) {
+  const int d = soff - p0;
+  const bool in = lane < nb && d >= 0 && d < 32;
+  const unsigned starts = __reduce_or_sync(kFull, in ? 1u << d : 0u);
+  const int before = __popc(__ballot_sync(kFull, lane < nb && soff < p0));
+  const int q = p - p0;
+  const unsigned upto = q >= 31 ? 0xffffffffu : (2u << q) - 1u;
+  return before + __popc(starts & upto) - 1;
 }
 
 // Copies the records of stream positions [p0, p0 + count) (count <= 32) into
@@ -321,7 +323,7 @@ template <int KB>
 __device__ __forceinline__ void load_records(int2* recs, const int2* __restrict__ rec, int soff,
                                              int64_t beg, int nb, int p0, int count, int lane) {
   const int p = p0 + lane;
-  const int r = rank_of<KB>(soff, nb, p);
+  const int r = rank_of<KB>(soff, nb, p0, p, lane);
   const int o = __shfl_sync(kFull, soff, r);
   const int64_t b = __shfl_sync(kFull, beg, r);
   if (lane < count) cp_async8(recs + (p % kRecBuf), rec + b + (p - o));
@@ -335,7 +337,7 @@ __device__ __forceinline__ void draw_stream_bits(uint2* srb, int soff, int64_t b
                                                  int p0, int T, int k4, uint2 seed, int lane) {
   constexpr int SRB = 32 / CPL;
   const int p = p0 + (lane < SRB ? lane : 0);  // lane u < SRB: position p0 + u
-  const int r = rank_of<KB>(soff, nb, p);
+  const int r = rank_of<KB>(soff, nb, p0, p, lane);
   const int o = __shfl_sync(kFull, soff, r);
   const int64_t b = __shfl_sync(kFull, beg, r);
   const int e = __shfl_sync(kFull, ep, r);
@@ -600,36 +602,34 @@ __device__ __forceinline__ void long_visit(float4 (&h)[CPL], typename Fmt<PR>::w
         if (lane == 0) Wscale[row] = sc;
         if (DEBUG && lane == 0) rec_count[beg + u] += 1;
       }
-      continue;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < B; ++i) {
-      if (i >= nu) break;
-      const int u = b * B + i;
-      const float se = s * e[i];
-      const float2 se2 = make_float2(se, se);
-      const int row = row_at(u);
-      w_t* wrow = W4 + int64_t(row) * pitch4;
-      float4 wn[CPL];
+      for (int i = 0; i < B; ++i) {
+        if (i >= nu) break;
+        const int u = b * B + i;
+        const float se = s * e[i];
+        const float2 se2 = make_float2(se, se);
+        const int row = row_at(u);
+        w_t* wrow = W4 + int64_t(row) * pitch4;
+        float4 wn[CPL];
 #pragma unroll
-      for (int cc = 0; cc < CPL; ++cc) {
-        wn[cc] = axpby(al2, w[i][cc], se2, h[cc]);  // a w_u + s e_u h_u
-        h[cc] = axpby(se2, w[i][cc], al2, h[cc]);   // a h_u + s e_u w_u
+        for (int cc = 0; cc < CPL; ++cc) {
+          wn[cc] = axpby(al2, w[i][cc], se2, h[cc]);  // a w_u + s e_u h_u
+          h[cc] = axpby(se2, w[i][cc], al2, h[cc]);   // a h_u + s e_u w_u
+        }
+        uint2 rb[CPL];
+        if constexpr (PR != kF32) {
+#pragma unroll
+          for (int cc = 0; cc < CPL; ++cc) rb[cc] = bits[i * CPL * 32 + lane + 32 * cc];
+        }
+        w_t out[CPL];
+        float scale = 1.f;
+        narrow_w<PR, CPL>(wn, rb, out, &scale);
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc)
+          if (lane + 32 * cc < k4) wrow[lane + 32 * cc] = out[cc];
+        if (DEBUG && lane == 0) rec_count[beg + u] += 1;
       }
-      uint2 rb[CPL];
-      if constexpr (PR != kF32) {
-#pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) rb[cc] = bits[i * CPL * 32 + lane + 32 * cc];
-      }
-      w_t out[CPL];
-      float scale = 1.f;
-      narrow_w<PR, CPL>(wn, rb, out, &scale);
-#pragma unroll
-      for (int cc = 0; cc < CPL; ++cc)
-        if (lane + 32 * cc < k4) wrow[lane + 32 * cc] = out[cc];
-      if constexpr (PR == kFP8)
-        if (lane == 0) Wscale[row] = scale;
-      if (DEBUG && lane == 0) rec_count[beg + u] += 1;
     }
   }
   cp_wait<0>();
@@ -1093,27 +1093,32 @@ __device__ __forceinline__ void batched_worker(const SgdParams& P, int q, unsign
       if constexpr (PR == kFP8)
         if (lane == 0) cp_async4(rsc + slot, Wscale + row);
     };
-    auto prefetch = [&](int pp, int row) {
-      const int slot = pp % R;
-      const unsigned m = __ballot_sync(kFull, lane < R && lane != slot && win == row);
-      if (m) {
-        // the latest of those positions: going back from pp - 1 the slots are
-        // slot - 1, ..., 0, R - 1, ..., slot + 1
-        const unsigned mm = (m | (m << R)) & ((1u << (slot + R)) - 1u);
-        if (lane == (31 - __clz(mm)) % R) fwd = slot;
-      } else {
-        copy_row(slot, row);
-      }
-      if (lane == slot) {
-        win = row;
-        fwd = -1;
-      }
-    };
     // one commit group per position: at tick t exactly R-1 groups are
-    // younger than position t's group, so cp.async.wait_group R-1 suffices
-    for (int pp = T0; pp < T0 + R - 1; ++pp) {
-      if (pp < T) prefetch(pp, recs[pp % kRecBuf].x);
-      cp_commit();
+    // younger than position t's group, so cp.async.wait_group R-1 suffices.
+    // The R-1 positions are decided together: lane L < R takes the position
+    // o = (L - T0) mod R of the cold start (slot L); lanes with the same row
+    // are found at once, a position with an earlier one of its row is not
+    // copied, and each position forwards to the next one of its row.
+    {
+      const int sh = int(unsigned(T0) % unsigned(R));
+      const int o = int(unsigned(lane - sh + R) % unsigned(R));
+      const bool live = lane < R && o < R - 1 && T0 + o < T;
+      const int row = live ? recs[unsigned(T0 + o) % kRecBuf].x : -(lane + 1);
+      const unsigned m = __match_any_sync(kFull, row);
+      const unsigned full = (1u << R) - 1u;
+      const unsigned mr = m & full;
+      const unsigned rot = ((mr >> sh) | (mr << (R - sh))) & full;  // bit o: order o
+      const bool has_src = live && (rot & ((1u << o) - 1u)) != 0u;
+      const unsigned later = live ? rot & ~((2u << o) - 1u) & full : 0u;
+      fwd = later ? int(unsigned(__ffs(later) - 1 + sh) % unsigned(R)) : -1;
+      win = live ? row : -1;
+      const unsigned copy = __ballot_sync(kFull, live && !has_src);
+      for (int q = 0; q < R - 1; ++q) {
+        const int slot = int(unsigned(q + sh) % unsigned(R));
+        const int rq = __shfl_sync(kFull, row, slot);
+        if ((copy >> slot) & 1u) copy_row(slot, rq);
+        cp_commit();
+      }
     }
 
     // ---- 5b. the stream
